@@ -1,0 +1,441 @@
+"""Pins of the FP64 oracle to what the paper and the mathematics fix.
+
+None of these compare the oracle with itself: every expected value comes from
+a closed form derived here, a formula the paper prints in another form (the
+explicit two- and three-layer pressures, the Pototsky mobility, the
+single-layer limits of the appendix), an invariant, or an independent
+linearisation of the scheme (tests/lsa.py).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from tests import lsa
+
+
+def _p(n=2, lattice=1, nx=8, ny=1, **kw):
+    p = dict(n=n, lattice=lattice, nx=nx, ny=ny, tau=1.0,
+             gamma=[0.01] * n, S=[[0.0] * (n - i) for i in range(n)],
+             mu=[1 / 6] * n, beta=[1.0] * n, nw=3, mw=2, hstar=0.1)
+    p.update(kw)
+    return p
+
+
+# --------------------------------------------------------------------------
+# wetting potential, Eq. (wetting_potential)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("nw,mw", [(3, 2), (4, 3), (9, 3), (6, 2)])
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_phi_at_k_hstar(nw, mw, k):
+    # the paper: phi_k(k h*) = 1 and phi'_k(k h*) = 0 for any exponent pair
+    p = _p(nw=nw, mw=mw, hstar=0.07)
+    assert oracle.phi(p, k, k * 0.07) == pytest.approx(1.0, abs=1e-15)
+    assert abs(oracle.dphi(p, k, k * 0.07)) < 1e-12
+
+
+def test_phi_hand_values():
+    # (3,2): phi_1(h) = 3 (h*/h)^2 - 2 (h*/h)^3; at h = 2h*: 3/4 - 2/8 = 1/2;
+    # phi_1'(h) = 6 [(h*/h)^3 - (h*/h)^2] / h; at h = 2h*: 6 (1/8 - 1/4)/(2h*)
+    p = _p(hstar=0.1)
+    assert oracle.phi(p, 1, 0.2) == pytest.approx(0.5, rel=1e-15)
+    assert oracle.dphi(p, 1, 0.2) == pytest.approx(-3.0 / (8 * 0.1), rel=1e-14)
+    # phi_2 at h = 4 h*: r = 1/2 as well
+    assert oracle.phi(p, 2, 0.4) == pytest.approx(0.5, rel=1e-15)
+    # vanishes far from the substrate (used by the appendix limits)
+    assert abs(oracle.phi(p, 1, 1e4)) < 1e-9 and abs(oracle.dphi(p, 1, 1e4)) < 1e-12
+
+
+@pytest.mark.parametrize("nw,mw", [(3, 2), (9, 3)])
+def test_dphi_is_derivative_of_phi(nw, mw):
+    p = _p(nw=nw, mw=mw, hstar=0.05)
+    for k in (1, 2, 4):
+        for h in (0.06, 0.13, 0.5, 2.0):
+            e = 1e-6 * h
+            fd = (oracle.phi(p, k, h + e) - oracle.phi(p, k, h - e)) / (2 * e)
+            assert oracle.dphi(p, k, h) == pytest.approx(fd, rel=1e-7, abs=1e-9)
+
+
+# --------------------------------------------------------------------------
+# spreading coefficients, Eq. (spreading_parameters)
+# --------------------------------------------------------------------------
+def _tension_table(n, rng):
+    G = n + 2
+    g = np.zeros((G, G))
+    for a in range(G):
+        for b in range(a + 1, G):
+            g[a, b] = g[b, a] = rng.uniform(0.01, 0.05)
+    return g
+
+
+def test_spreading_two_layers_by_hand():
+    g = np.zeros((4, 4))
+    vals = {(0, 1): 0.031, (0, 2): 0.043, (0, 3): 0.05, (1, 2): 0.011,
+            (1, 3): 0.027, (2, 3): 0.02}
+    for (a, b), v in vals.items():
+        g[a, b] = g[b, a] = v
+    S, gam = oracle.spreading_from_tensions(_p(n=2), g.ravel())
+    # S_01 = g02 - g01 - g12, S_11 = g13 - g12 - g23,
+    # S_02 = g03 + g12 - g02 - g13
+    assert S[0][0] == pytest.approx(0.043 - 0.031 - 0.011, abs=1e-16)
+    assert S[1][0] == pytest.approx(0.027 - 0.011 - 0.02, abs=1e-16)
+    assert S[0][1] == pytest.approx(0.05 + 0.011 - 0.043 - 0.027, abs=1e-16)
+    assert gam == [0.011, 0.02]
+
+
+def test_spreading_young_sessile_types():
+    # Young's law (Eq. youngs_law) for the droplet types of the angle section:
+    # the film's spreading coefficient is gamma_lv (cos theta - 1).
+    rng = np.random.default_rng(5)
+    g = _tension_table(2, rng)
+    S, _ = oracle.spreading_from_tensions(_p(n=2), g.ravel())
+    # type 1: sv = 02, sl = 01, lv = 12 -> S_01
+    assert S[0][0] == pytest.approx(g[1, 2] * ((g[0, 2] - g[0, 1]) / g[1, 2] - 1))
+    # type 3 / lens bottom: liquid 2 on liquid 1 in gas, sv=13, sl=12, lv=23
+    assert S[1][0] == pytest.approx(g[2, 3] * ((g[1, 3] - g[1, 2]) / g[2, 3] - 1))
+
+
+# --------------------------------------------------------------------------
+# pressures vs the explicit two- and three-layer forms printed in the paper
+# --------------------------------------------------------------------------
+def _rand_pressure_case(n, seed):
+    rng = np.random.default_rng(seed)
+    p = _p(n=n, hstar=0.08, nw=3, mw=2)
+    p["gamma"] = list(rng.uniform(0.005, 0.02, n))
+    p["S"] = [list(rng.uniform(-1e-3, 1e-3, n - i)) for i in range(n)]
+    h = rng.uniform(0.1, 1.5, n)
+    gzx = rng.uniform(-0.3, 0.3, n)
+    gzy = rng.uniform(-0.3, 0.3, n)
+    lz = rng.uniform(-0.05, 0.05, n)
+    return p, h, gzx, gzy, lz
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_pressure_two_layers_explicit(seed):
+    p, h, gzx, gzy, lz = _rand_pressure_case(2, seed)
+    La, Pi, pr = oracle.pressures(p, h, gzx, gzy, lz)
+    S = p["S"]
+    z1, z2 = h[0], h[0] + h[1]
+    g1 = gzx[0] ** 2 + gzy[0] ** 2
+    phi = lambda i, k, d: S[i][k - 1] * lsa.phi_k(p, k, d)
+    dphi = lambda i, k, d: S[i][k - 1] * lsa.dphi_k(p, k, d)
+    # p1 - p2 and p2 - p_atm as printed in the two-layer section
+    d1 = (dphi(0, 1, z1) - dphi(1, 1, z2 - z1) * (1 + g1 / 2)
+          - (p["gamma"][0] + phi(1, 1, z2 - z1)) * lz[0])
+    d2 = dphi(1, 1, z2 - z1) * (1 + g1 / 2) + dphi(0, 2, z2) - p["gamma"][1] * lz[1]
+    assert La[0] + Pi[0] == pytest.approx(d1, rel=1e-12, abs=1e-16)
+    assert La[1] + Pi[1] == pytest.approx(d2, rel=1e-12, abs=1e-16)
+    # p_i - p_atm = sum_{j >= i} jumps
+    assert pr[1] == pytest.approx(d2, rel=1e-12, abs=1e-16)
+    assert pr[0] == pytest.approx(d1 + d2, rel=1e-12, abs=1e-16)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_pressure_three_layers_explicit(seed):
+    p, h, gzx, gzy, lz = _rand_pressure_case(3, 100 + seed)
+    La, Pi, pr = oracle.pressures(p, h, gzx, gzy, lz)
+    S = p["S"]
+    h1, h2, h3 = h
+    z2, z3 = h1 + h2, h1 + h2 + h3
+    g = [gzx[i] ** 2 + gzy[i] ** 2 for i in range(3)]
+    g0 = 0.0  # flat substrate
+    phi = lambda i, k, d: S[i][k - 1] * lsa.phi_k(p, k, d)
+    dphi = lambda i, k, d: S[i][k - 1] * lsa.dphi_k(p, k, d)
+    G = p["gamma"]
+    # the three pressure jumps printed in the three-layer section
+    d1 = (-(G[0] + phi(1, 1, h2) + phi(1, 2, h2 + h3)) * lz[0]
+          - (dphi(1, 1, h2) + dphi(1, 2, h2 + h3)) * (1 + g[0] / 2)
+          + dphi(0, 1, h1) * (1 + g0 / 2))
+    d2 = (-(G[1] + phi(2, 1, h3)) * lz[1] - dphi(2, 1, h3) * (1 + g[1] / 2)
+          + dphi(0, 2, z2) * (1 + g0 / 2) + dphi(1, 1, h2) * (1 + g[0] / 2))
+    d3 = (-G[2] * lz[2] + dphi(0, 3, z3) * (1 + g0 / 2)
+          + dphi(1, 2, h2 + h3) * (1 + g[0] / 2) + dphi(2, 1, h3) * (1 + g[1] / 2))
+    for got, want in zip(La + Pi, (d1, d2, d3)):
+        assert got == pytest.approx(want, rel=1e-12, abs=1e-16)
+    assert pr == pytest.approx([d1 + d2 + d3, d2 + d3, d3], rel=1e-12, abs=1e-16)
+
+
+def test_pressure_limits_of_appendix():
+    """Limit cases of the two-layer model (appendix).
+
+    h2 -> h*: p1 - p2 = S01 phi'(z1) - (g13 - g23) lap z1 and the upper layer
+    carries only the combined-layer term; h1 -> h*: p1 - p2 = -S11 phi'(h2)
+    with S11 = g13 - g12 - g23 and S02 + S11 = g03 - g02 - g23.
+    """
+    rng = np.random.default_rng(11)
+    g = _tension_table(2, rng)
+    p = _p(n=2, hstar=0.07)
+    S, gam = oracle.spreading_from_tensions(p, g.ravel())
+    p["S"], p["gamma"] = S, gam
+    hs = p["hstar"]
+    lz = np.array([0.013, 0.013])  # uniform h2 = h*: both interfaces share lap
+    zero = np.zeros(2)
+    gz = np.array([0.2, 0.2])
+    h = np.array([0.9, hs])
+    La, Pi, _ = oracle.pressures(p, h, gz, zero, lz)
+    d1 = (g[0, 2] - g[0, 1] - g[1, 2]) * lsa.dphi_k(p, 1, 0.9) - (g[1, 3] - g[2, 3]) * lz[0]
+    assert La[0] + Pi[0] == pytest.approx(d1, rel=1e-12)
+    d2 = S[0][1] * lsa.dphi_k(p, 2, 0.9 + hs) - g[2, 3] * lz[1]
+    assert La[1] + Pi[1] == pytest.approx(d2, rel=1e-12)
+    # h1 = h*: lap z1 = 0 and grad z1 = 0 (uniform lower precursor)
+    h = np.array([hs, 0.8])
+    lz = np.array([0.0, 0.02])
+    La, Pi, _ = oracle.pressures(p, h, zero, zero, lz)
+    d1 = -(g[1, 3] - g[1, 2] - g[2, 3]) * lsa.dphi_k(p, 1, 0.8)
+    assert La[0] + Pi[0] == pytest.approx(d1, rel=1e-12)
+    assert S[0][1] + S[1][0] == pytest.approx(g[0, 3] - g[0, 2] - g[2, 3], abs=1e-16)
+
+
+# --------------------------------------------------------------------------
+# friction, Eqs. (u_ansatz)-(friction_force)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("seed", range(8))
+def test_friction_single_layer_closed_form(seed):
+    """n = 1: u = a z^2 + b z + c with u(-beta) = 0, u'(h) = 0 and flux J.
+
+    Then b = -2 a h, c = -a (2 h beta + beta^2) and
+    J = a (h^3/3 - h^3 - 2 h^2 beta - beta^2 h) so the friction is
+    2 mu h a = -6 mu J / (2 h^2 + 6 h beta + 3 beta^2); for beta = 0 this is
+    -3 mu J / h^2, i.e. the single-layer mobility h^3 / (3 mu).
+    """
+    rng = np.random.default_rng(seed)
+    h, mu, beta, J = rng.uniform(0.05, 2), rng.uniform(0.05, 1), rng.uniform(0, 2), rng.normal()
+    if seed == 0:
+        beta = 0.0
+    p = _p(n=1, mu=[mu], beta=[beta])
+    Rx, Ry = oracle.friction(p, [h], [J], [-2 * J])
+    want = -6 * mu * J / (2 * h * h + 6 * h * beta + 3 * beta * beta)
+    assert Rx[0] == pytest.approx(want, rel=1e-13)
+    assert Ry[0] == pytest.approx(-2 * want, rel=1e-13)
+
+
+def _K_oracle(p, h):
+    n = int(p["n"])
+    K = np.zeros((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        K[:, j] = oracle.friction(p, h, e, e)[0]
+    return K
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_friction_two_layer_pototsky_mobility(seed):
+    """No-slip two-layer mobility, Eq. (mobility_pototski).
+
+    With M = -K^-1 T (T_ij = h_i for j >= i), [[1,0],[1,1]] M must equal the
+    symmetric Pototsky matrix printed in the two-layer section.
+    """
+    rng = np.random.default_rng(seed)
+    h = rng.uniform(0.05, 1.5, 2)
+    mu = rng.uniform(0.05, 1.0, 2)
+    p = _p(n=2, mu=list(mu), beta=[0.0, 0.0])
+    K = _K_oracle(p, h)
+    T = np.array([[h[0], h[0]], [0.0, h[1]]])
+    M = -np.linalg.solve(K, T)
+    Mt = np.array([[1, 0], [1, 1]]) @ M
+    z1, z2 = h[0], h[0] + h[1]
+    m1, m2 = mu
+    want = np.array([
+        [z1 ** 3 / (3 * m1), z1 ** 3 / (3 * m1) + z1 ** 2 * (z2 - z1) / (2 * m1)],
+        [z1 ** 3 / (3 * m1) + z1 ** 2 * (z2 - z1) / (2 * m1),
+         (z2 - z1) ** 3 * (m1 - m2) / (3 * m1 * m2) + z2 ** 3 / (3 * m1)]])
+    np.testing.assert_allclose(Mt, want, rtol=1e-11, atol=1e-14)
+    # printed M_11, M_12 of Eq. (mobility_2) directly
+    assert M[0, 0] == pytest.approx(z1 ** 3 / (3 * m1), rel=1e-11)
+    assert M[0, 1] == pytest.approx(z1 ** 3 / (3 * m1) + z1 ** 2 * (z2 - z1) / (2 * m1), rel=1e-11)
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5])
+def test_friction_uniform_stack_is_one_film(n):
+    """Equal viscosities, no interfacial slip, one pressure gradient G in
+    every layer: the stack is a single film of thickness H = z_n with
+    u(z) = (G/mu)(z^2/2 - H z - beta^2/2 - H beta) (u(-beta) = 0, u'(H) = 0).
+    The friction on layer i must then be h_i G for the layer fluxes of u."""
+    rng = np.random.default_rng(n)
+    h = rng.uniform(0.1, 0.8, n)
+    mu, beta1, G = 0.3, 0.7, -0.37
+    p = _p(n=n, mu=[mu] * n, beta=[beta1] + [0.0] * (n - 1))
+    z = np.concatenate([[0.0], np.cumsum(h)])
+    H = z[-1]
+    U = lambda s: (G / mu) * (s ** 3 / 6 - H * s ** 2 / 2 - (beta1 ** 2 / 2 + H * beta1) * s)
+    J = np.array([U(z[i + 1]) - U(z[i]) for i in range(n)])
+    Rx, _ = oracle.friction(p, h, J, J)
+    np.testing.assert_allclose(Rx, h * G, rtol=1e-11, atol=1e-14)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("seed", range(4))
+def test_friction_matches_stress_integration(n, seed):
+    """Random viscosities and slips: the literal D solve equals the friction
+    from integrating the shear stress (tests/lsa.py, independent of D)."""
+    rng = np.random.default_rng(1000 * n + seed)
+    h = rng.uniform(0.05, 1.5, n)
+    mu = list(rng.uniform(0.05, 1.0, n))
+    beta = list(rng.uniform(0.0, 1.5, n))
+    p = _p(n=n, mu=mu, beta=beta)
+    np.testing.assert_allclose(_K_oracle(p, h), lsa.friction_matrix(p, h),
+                               rtol=1e-9, atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# equilibrium, Eq. (equilibrium_distribution)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("lat", [1, 2])
+def test_equilibrium_moments(lat):
+    p = _p(lattice=lat)
+    cx, cy, w = lsa.lattice(p)
+    rng = np.random.default_rng(lat)
+    for _ in range(10):
+        h = rng.uniform(0.05, 2)
+        Ux, Uy = rng.normal(0, 0.1), (rng.normal(0, 0.1) if lat == 2 else 0.0)
+        f = oracle.equilibrium(p, h, Ux, Uy)
+        assert f.sum() == pytest.approx(h, rel=1e-14)
+        assert (cx * f).sum() == pytest.approx(h * Ux, rel=1e-13, abs=1e-16)
+        assert (cy * f).sum() == pytest.approx(h * Uy, rel=1e-13, abs=1e-16)
+        assert (cx * cx * f).sum() == pytest.approx(h * Ux * Ux, rel=1e-12, abs=1e-16)
+        assert (cx * cy * f).sum() == pytest.approx(h * Ux * Uy, rel=1e-12, abs=1e-16)
+        assert (cy * cy * f).sum() == pytest.approx(h * Uy * Uy, rel=1e-12, abs=1e-16)
+    # at rest all mass sits in the rest population (no w_k h term)
+    f = oracle.equilibrium(p, 0.7, 0.0, 0.0)
+    assert f[0] == 0.7 and np.all(f[1:] == 0.0)
+
+
+@pytest.mark.parametrize("lat,tau", [(1, 1.0), (2, 1.0), (2, 0.8), (1, 1.7)])
+def test_uniform_state_momentum_update(lat, tau):
+    """On a uniform state all gradients vanish, so after one step
+    h' = h and J' = J + K J: the forcing term carries exactly the force and
+    the collision conserves h and J for any tau."""
+    n = 3
+    p = workloads.random_params(7, n, lat, 5, 4 if lat == 2 else 1, tau=tau)
+    rng = np.random.default_rng(3)
+    q = 3 if lat == 1 else 9
+    f = np.zeros((n, q, p["ny"], p["nx"]))
+    cell = rng.uniform(-0.01, 0.01, (n, q))
+    cell[:, 0] = rng.uniform(0.5, 1.0, n)
+    f[:] = cell[:, :, None, None]
+    h, Jx, Jy = oracle.moments(p, f)
+    g = oracle.step(p, f)
+    h2, Jx2, Jy2 = oracle.moments(p, g)
+    hc, jx, jy = h[:, 0, 0], Jx[:, 0, 0], Jy[:, 0, 0]
+    K = lsa.friction_matrix(p, hc)
+    np.testing.assert_allclose(h2[:, 0, 0], hc, rtol=1e-14)
+    np.testing.assert_allclose(Jx2[:, 0, 0], jx + K @ jx, rtol=1e-9, atol=1e-15)
+    np.testing.assert_allclose(Jy2[:, 0, 0], jy + K @ jy, rtol=1e-9, atol=1e-15)
+
+
+# --------------------------------------------------------------------------
+# invariants of the scheme
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("lat", [1, 2])
+def test_flat_film_is_steady_bit_exact(lat):
+    p = workloads.random_params(3, 3, lat, 9, 7 if lat == 2 else 1)
+    h0 = np.array([0.9, 0.4, 0.7])
+    h = np.broadcast_to(h0[:, None, None], (3, p["ny"], p["nx"])).copy()
+    f = oracle.init(p, h.ravel())
+    g = oracle.run(p, f, 50)
+    assert np.array_equal(f, g)
+
+
+@pytest.mark.parametrize("lat", [1, 2])
+def test_mass_conserved_per_layer(lat):
+    p = workloads.random_params(4, 3, lat, 24, 20 if lat == 2 else 1)
+    f = workloads.random_populations(9, p, 0.5, 1.0, 1e-3)
+    m0 = oracle.heights(p, f).sum(axis=(1, 2))
+    g = oracle.run(p, f, 200)
+    m1 = oracle.heights(p, g).sum(axis=(1, 2))
+    np.testing.assert_allclose(m1, m0, rtol=1e-13)
+
+
+def test_translation_equivariance_bit_exact():
+    p = workloads.random_params(5, 3, 2, 12, 10)
+    f = workloads.random_populations(6, p, 0.5, 1.0, 1e-3)
+    g = oracle.run(p, f, 5)
+    fs = np.roll(f, (3, -5), axis=(2, 3))
+    gs = oracle.run(p, fs, 5)
+    assert np.array_equal(np.roll(g, (3, -5), axis=(2, 3)), gs)
+
+
+def test_mirror_symmetry():
+    # x -> -x maps direction k to its mirror image; results agree to round-off
+    p = workloads.random_params(8, 2, 2, 10, 9)
+    cx, cy, _ = lsa.D2Q9
+    mirror = [int(np.where((cx == -cx[k]) & (cy == cy[k]))[0][0]) for k in range(9)]
+    f = workloads.random_populations(12, p, 0.5, 1.0, 1e-3)
+    fm = f[:, mirror, :, ::-1].copy()
+    g = oracle.run(p, f, 4)
+    gm = oracle.run(p, fm, 4)
+    np.testing.assert_allclose(gm, g[:, mirror, :, ::-1], rtol=0, atol=1e-14)
+
+
+# --------------------------------------------------------------------------
+# linear stability: the oracle against the independent linearisation
+# --------------------------------------------------------------------------
+def _lsa_case(lat, n, seed, tau):
+    p = workloads.random_params(seed, n, lat, 32 if lat == 1 else 16,
+                                1 if lat == 1 else 12, tau=tau)
+    p["mu"] = [m * 0.4 for m in p["mu"]]
+    return p
+
+
+@pytest.mark.parametrize("lat,n,seed,tau,mode", [
+    (1, 2, 21, 1.0, (3, 0)), (1, 3, 22, 0.9, (5, 0)),
+    (2, 2, 23, 1.0, (2, 1)), (2, 3, 24, 1.0, (1, 3)), (2, 3, 25, 1.3, (3, 2)),
+])
+def test_single_mode_follows_linearised_step(lat, n, seed, tau, mode):
+    p = _lsa_case(lat, n, seed, tau)
+    rng = np.random.default_rng(seed)
+    h0 = rng.uniform(0.5, 1.1, n)
+    amps = rng.uniform(-1, 1, n)
+    eps, steps = 1e-6, 60
+    h = workloads.single_mode_heights(p, h0, amps, mode, eps)
+    f = oracle.init(p, h.ravel())
+    g = oracle.run(p, f, steps)
+    nx, ny = p["nx"], p["ny"]
+    q = (2 * np.pi * mode[0] / nx, 2 * np.pi * mode[1] / ny)
+    y, x = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    basis = np.exp(-1j * (q[0] * x + q[1] * y)) / (nx * ny)
+    proj = lambda a: np.einsum("ikyx,yx->ik", a, basis).ravel()
+    v0 = proj(f)
+    G = lsa.step_matrix(p, h0, q)
+    assert np.max(np.abs(np.linalg.eigvals(G))) < 1.05  # a stable parameter set
+    want = np.linalg.matrix_power(G, steps) @ v0
+    got = proj(g)
+    err = np.linalg.norm(got - want) / np.linalg.norm(want)
+    assert err < 1e-6, err
+
+
+def test_growth_rate_matches_continuum_lsa():
+    """Eq. (linear_thin_film_equation): at small q the slowest LBM mode grows
+    at the rate of -q^2 M E (continuum mobility and pressure symbols)."""
+    p = dict(workloads.film2_d1q3_params(256))
+    # a clearly unstable two-layer film (S_01 < 0), as in the LSA section
+    p["S"] = [[-4e-3, 0.0], [-2e-3]]
+    p["hstar"] = 0.1
+    h0 = np.array([0.35, 0.3])
+    for mode in (2, 3):
+        q = 2 * np.pi * mode / p["nx"]
+        lam = np.linalg.eigvals(lsa.step_matrix(p, h0, (q, 0.0)))
+        lbm = np.max(np.log(np.abs(lam)))
+        cont = np.max(lsa.continuum_growth(p, h0, q).real)
+        assert cont > 0
+        assert lbm == pytest.approx(cont, rel=0.05)
+    # the oracle's own growth of that mode follows the continuum rate too:
+    # start on the growing eigenvector (a real synthetic population field)
+    mode = 3
+    q = 2 * np.pi * mode / p["nx"]
+    w, V = np.linalg.eig(lsa.step_matrix(p, h0, (q, 0.0)))
+    top = np.argmax(np.abs(w))
+    x = np.arange(p["nx"])
+    flat = np.broadcast_to(h0[:, None, None], (2, 1, p["nx"])).copy()
+    f = oracle.init(p, flat.ravel())
+    v = V[:, top] / np.abs(V[:, top]).max()
+    f += 1e-7 * np.real(v.reshape(2, 3, 1, 1) * np.exp(1j * q * x))
+    steps = 3000
+    g = oracle.run(p, f, steps)
+    amp = lambda a: np.abs((oracle.heights(p, a)[0, 0] - h0[0]) @ np.exp(-1j * q * x))
+    rate = math.log(amp(g) / amp(f)) / steps
+    cont = np.max(lsa.continuum_growth(p, h0, q).real)
+    assert rate == pytest.approx(cont, rel=0.05)

@@ -1,0 +1,136 @@
+"""Seeded synthetic inputs shared by the oracle checks, the CUDA tests and the
+benchmark.
+
+This module only produces input data: parameter sets and initial height
+fields / population arrays drawn from seeded generators. It holds none of the
+arithmetic of the lattice Boltzmann step (no pressures, friction, equilibria
+or streaming), so it can feed both the oracle and the CUDA path.
+
+Parameter dicts use the layout both bindings accept:
+    n, lattice (1 = D1Q3, 2 = D2Q9), nx, ny, tau,
+    gamma[n]     gamma_{i,i+1} for i = 1..n (n+1 is the gas),
+    S[i][k-1]    spreading coefficient S_{ik}, i = 0..n-1, k = 1..n-i,
+    mu[n], beta[n], nw, mw, hstar.
+
+Workload recipes (the paper fixes no grid sizes or values for its timed
+runs; these stand in for its two- and three-layer spinodal set-ups):
+  * two-layer pseudo-2D film: D1Q3, 512 periodic cells, h1 = h2 = 1 plus
+    seeded uniform noise of +-1e-3, gamma 0.01 / 0.01, mu = 1/6, slip 1,
+    exponents (3, 2), h* = 0.1, contact angle 20 degrees;
+  * three-layer pseudo-3D spinodal film: D2Q9, 1024 x 1024 periodic cells,
+    means 1.0 / 0.8 / 0.6 plus seeded Gaussian noise sigma = 1e-3, gamma
+    0.01 / 0.008 / 0.006, mu = (1, 2, 4) / 6, slip 1, (3, 2), h* = 0.07,
+    contact angle 20 degrees.
+A contact angle theta is turned into the one-layer spreading coefficients by
+Young's law, cos(theta) = 1 + S_{i1} / gamma_{i+1,i+2}; multi-layer
+coefficients S_{ik}, k >= 2, are zero as in the paper's three-layer runs.
+"""
+import math
+
+import numpy as np
+
+DEG = math.pi / 180.0
+
+
+def _young_spreading(gamma, theta_deg, n):
+    c = math.cos(theta_deg * DEG) - 1.0
+    S = []
+    for i in range(n):
+        row = [0.0] * (n - i)
+        row[0] = gamma[i] * c
+        S.append(row)
+    return S
+
+
+def film2_d1q3_params(nx=512):
+    """Two-layer pseudo-2D film on a D1Q3 lattice."""
+    n = 2
+    gamma = [0.01, 0.01]
+    return dict(n=n, lattice=1, nx=int(nx), ny=1, tau=1.0, gamma=gamma,
+                S=_young_spreading(gamma, 20.0, n), mu=[1 / 6, 1 / 6],
+                beta=[1.0, 1.0], nw=3, mw=2, hstar=0.1)
+
+
+def film2_d1q3_heights(nx=512, seed=1):
+    rng = np.random.default_rng(seed)
+    return 1.0 + rng.uniform(-1e-3, 1e-3, size=(2, 1, int(nx)))
+
+
+def film3_d2q9_params(nx=1024, ny=1024):
+    """Three-layer pseudo-3D spinodal film on a D2Q9 lattice."""
+    n = 3
+    gamma = [0.01, 0.008, 0.006]
+    return dict(n=n, lattice=2, nx=int(nx), ny=int(ny), tau=1.0, gamma=gamma,
+                S=_young_spreading(gamma, 20.0, n),
+                mu=[1 / 6, 2 / 6, 4 / 6], beta=[1.0, 1.0, 1.0], nw=3, mw=2,
+                hstar=0.07)
+
+
+def film3_d2q9_heights(nx=1024, ny=1024, seed=2):
+    rng = np.random.default_rng(seed)
+    means = np.array([1.0, 0.8, 0.6]).reshape(3, 1, 1)
+    return means + rng.normal(0.0, 1e-3, size=(3, int(ny), int(nx)))
+
+
+def random_params(seed, n, lattice, nx, ny=1, tau=1.0, multilayer_S=True):
+    """Seeded random parameter set, with all S_{ik} populated when asked.
+
+    Tensions, viscosities and slips are drawn log-uniformly; exponents are
+    drawn from a few integer pairs with nw > mw.
+    """
+    rng = np.random.default_rng(seed)
+    gamma = list(np.exp(rng.uniform(np.log(2e-3), np.log(2e-2), n)))
+    mu = list(np.exp(rng.uniform(np.log(0.05), np.log(0.8), n)))
+    beta = list(rng.uniform(0.3, 1.5, n))
+    S = []
+    for i in range(n):
+        row = []
+        for k in range(1, n - i + 1):
+            if k == 1 or multilayer_S:
+                row.append(float(rng.uniform(-1.0, 0.5) * 1e-3))
+            else:
+                row.append(0.0)
+        S.append(row)
+    nw, mw = [(3, 2), (4, 3), (9, 3), (6, 2)][int(rng.integers(0, 4))]
+    return dict(n=n, lattice=lattice, nx=int(nx), ny=int(ny), tau=float(tau),
+                gamma=[float(g) for g in gamma], S=S,
+                mu=[float(m) for m in mu], beta=[float(b) for b in beta],
+                nw=nw, mw=mw, hstar=float(rng.uniform(0.05, 0.1)))
+
+
+def random_heights(seed, p, lo=0.3, hi=1.2, noise=1e-2):
+    """Layer means in [lo, hi] plus seeded uniform noise of +-noise."""
+    rng = np.random.default_rng(seed)
+    n, ny, nx = int(p["n"]), int(p["ny"]), int(p["nx"])
+    means = rng.uniform(lo, hi, size=(n, 1, 1))
+    return means + rng.uniform(-noise, noise, size=(n, ny, nx))
+
+
+def random_populations(seed, p, h_lo=0.3, h_hi=1.2, amp=2e-3):
+    """A seeded non-equilibrium population array f[n][Q][ny][nx].
+
+    The rest population carries a random layer thickness in [h_lo, h_hi];
+    moving populations carry independent uniform values in [-amp, amp].
+    Used as a generic state for single-step comparisons.
+    """
+    rng = np.random.default_rng(seed)
+    n, ny, nx = int(p["n"]), int(p["ny"]), int(p["nx"])
+    q = 3 if int(p["lattice"]) == 1 else 9
+    f = rng.uniform(-amp, amp, size=(n, q, ny, nx))
+    f[:, 0] = rng.uniform(h_lo, h_hi, size=(n, ny, nx))
+    return f
+
+
+def single_mode_heights(p, h0, amps, mode, eps):
+    """h_i = h0_i + eps * amps_i * cos(2 pi (mx x / nx + my y / ny)).
+
+    A single Fourier mode used by the linear-stability checks.
+    """
+    n, ny, nx = int(p["n"]), int(p["ny"]), int(p["nx"])
+    mx, my = mode
+    y, x = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    ph = 2 * np.pi * (mx * x / nx + my * y / ny)
+    h = np.empty((n, ny, nx))
+    for i in range(n):
+        h[i] = h0[i] + eps * amps[i] * np.cos(ph)
+    return h
