@@ -1,0 +1,367 @@
+"""Benchmark of the fused multilayer shallow-water LBM step on GB300.
+
+Workload: the three-layer pseudo-3D spinodal film (D2Q9, 1024 x 1024
+periodic cells, means 1.0 / 0.8 / 0.6 plus seeded Gaussian noise 1e-3,
+gamma 0.01 / 0.008 / 0.006, mu = (1, 2, 4) / 6, slip 1, wetting exponents
+(3, 2), h* = 0.07, contact angle 20 degrees), FP32 populations.
+
+A benchmark step is one LBM time step (one fused kernel launch) over the
+whole lattice. Metric: layer-site updates per second,
+LSU/s = n_layers * nx * ny * steps / time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Own arm: inputs resident in HBM, each timed step bracketed by CUDA events on
+the solver's stream; between timed steps the L2 is flushed (a 256 MiB write
+followed by a 256 MiB read, so the next step starts from a cold, clean L2).
+The e2e figure goes through the public API with host buffers: every step
+uploads the heights from pinned memory (mlswlbm_set_heights), advances one
+step and reads the heights back (mlswlbm_get_heights).
+
+Reference arm (--impl reference): the FP64 CPU oracle on the host cores, one
+oracle step per benchmark step on a 128 x 128 patch with the same recipe.
+Under torchrun only rank 0 runs it.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+NX = NY = 1024
+N_LAYERS = 3
+Q = 9
+BYTES_PER_LSU = 2 * Q * 4          # read + write of every FP32 population
+METRIC = "layer-site updates/s"
+UNIT = "LSU/s"
+WORKLOAD = "3-layer D2Q9 spinodal film, 1024x1024 periodic, FP32 populations"
+FALLBACK_HBM_GBS = 6800.0
+KERNEL_SOURCES = ["paper_2409_16659_gb300/csrc/step_kernels.cu",
+                  "paper_2409_16659_gb300/csrc/physics.cuh"]
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def config_dict(extra=None):
+    c = {"workload": WORKLOAD, "n_layers": N_LAYERS, "lattice": "D2Q9", "nx": NX, "ny": NY,
+         "cells": NX * NY, "layer_sites_per_step": N_LAYERS * NX * NY,
+         "l2": "flushed between timed steps (256 MiB write + 256 MiB read); "
+               "per-step working set 226 MB > 129 MB L2",
+         "parallelism": "replicas (one independent lattice per GPU)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            v = float(json.load(fh)["hbm_gbs"])
+        return v, "measured (MEASURED_PEAKS.json hbm_gbs, STREAM-style copy)"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback (no MEASURED_PEAKS.json)"
+
+
+def ncu_traffic():
+    """DRAM bytes per launch of the step kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    want = kernel_hash()
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 4 and not line.startswith("#") and parts[0] == "step_d2q9_film3_1024" \
+                and parts[1] == want:
+            return float(parts[2])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.tmp = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=self.tmp, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.tmp.flush()
+        rows = []
+        with open(self.tmp.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.tmp.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_sample(seconds=12.0, side=256):
+    """The FP64 oracle on a bounded patch of the same workload recipe."""
+    import oracle
+    p = workloads.film3_d2q9_params(side, side)
+    h0 = workloads.film3_d2q9_heights(side, side)
+    f = oracle.init(p, h0.ravel())
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        f = oracle.step(p, f)
+        steps += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    lsu = N_LAYERS * side * side * steps / dt
+    return {"value": lsu, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "FP64 C oracle, 1 thread, %d steps on a %dx%d patch of the 3-layer "
+                      "D2Q9 film (same parameters), %.1f s" % (steps, side, side, dt)}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    import oracle
+    side = 128
+    p = workloads.film3_d2q9_params(side, side)
+    f = oracle.init(p, workloads.film3_d2q9_heights(side, side).ravel())
+    for _ in range(args.warmup):
+        f = oracle.step(p, f)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f = oracle.step(p, f)
+    dt = time.perf_counter() - t0
+    lsu = N_LAYERS * side * side * args.steps / dt
+    sample = ("FP64 C oracle, 1 thread, one oracle step per benchmark step on a %dx%d patch "
+              "of the 3-layer D2Q9 film (same parameters)" % (side, side))
+    line = {"impl": "reference", "metric": METRIC, "value": lsu, "unit": UNIT,
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict({"sample_nx": side, "sample_ny": side}),
+            "cpu_baseline": {"value": lsu, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": lsu, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_own(args):
+    import torch
+    ws, rank, local = dist_setup()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    from paper_2409_16659_gb300 import mlswlbm as B
+
+    p = workloads.film3_d2q9_params(NX, NY)
+    h0 = workloads.film3_d2q9_heights(NX, NY, seed=2 + rank).astype(np.float32)
+    stream = torch.cuda.current_stream()
+    solver = B.Solver(p, h0, stream=stream)
+    lsu_step = N_LAYERS * NX * NY
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ---- warm-up ----------------------------------------------------------
+    for _ in range(args.warmup):
+        solver.step(1)
+    torch.cuda.synchronize()
+
+    flush_w = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB
+    flush_r = torch.ones(64 * 1024 * 1024, dtype=torch.float32, device="cuda")    # 256 MiB
+    sink = torch.zeros(1, dtype=torch.float32, device="cuda")
+
+    def flush(i):
+        flush_w.fill_(float(i & 1023))
+        sink.add_(flush_r.sum())
+
+    # ---- timed region: K steps, L2 flushed between them --------------------
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    sampler = ClockSampler(dev) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    launches0 = solver.launch_count()
+    barrier()
+    for i in range(args.steps):
+        flush(i)
+        starts[i].record(stream)
+        solver.step(1)
+        ends[i].record(stream)
+    barrier()
+    launches = solver.launch_count() - launches0
+    clocks = sampler.stop() if sampler else None
+    step_ms = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])
+    total_s = float(step_ms.sum()) / 1e3
+
+    # ---- steady state: back-to-back steps, no flush (context only) --------
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    solver.step(args.steps)
+    e1.record(stream)
+    barrier()
+    steady_s = e0.elapsed_time(e1) / 1e3
+
+    # ---- e2e through the public API with pinned host buffers ---------------
+    h_host = torch.from_numpy(h0.reshape(-1)).pin_memory()
+    h_out = torch.empty(h_host.numel(), dtype=torch.float32).pin_memory()
+    h_host_np, h_out_np = h_host.numpy(), h_out.numpy().reshape(N_LAYERS, NY, NX)
+    k_e2e = max(3, min(args.steps, 200))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        solver.set_heights(h_host_np)
+        solver.step(1)
+        solver.get_heights(h_out_np)
+    t1 = time.perf_counter()
+    e2e_s = t1 - t0
+    assert np.isfinite(h_out_np).all()
+    status = solver.status()
+    solver.close()
+
+    tot = torch.tensor([total_s, steady_s, e2e_s], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        torch.distributed.all_reduce(tot, op=torch.distributed.ReduceOp.MAX)
+    total_s, steady_s, e2e_s = [float(v) for v in tot.cpu()]
+
+    if rank == 0:
+        value = ws * lsu_step * args.steps / total_s
+        avg_launch_s = total_s / args.steps
+        bytes_alg = BYTES_PER_LSU * lsu_step
+        peak, peak_src = hbm_peak()
+        achieved = bytes_alg / avg_launch_s / 1e9
+        traffic = ncu_traffic()
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * avg_launch_s, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config_dict(),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "step_d2q9_kernel<3,8,2,true>",
+                         "bytes_per_launch_algorithmic": bytes_alg, "peak_source": peak_src},
+            "e2e": {"value": ws * lsu_step * k_e2e / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": int(h_host.numel() * 4),
+                    "d2h_bytes_per_step": int(h_out.numel() * 4), "steps": k_e2e,
+                    "api": "mlswlbm_set_heights + mlswlbm_step(1) + mlswlbm_get_heights"},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+            "steady_state": {"value": ws * lsu_step * args.steps / steady_s,
+                             "ms_per_step": 1e3 * steady_s / args.steps,
+                             "note": "back-to-back steps without L2 flush"},
+            "step_ms_p50": float(np.median(step_ms)), "step_ms_min": float(step_ms.min()),
+            "status": B.mlswlbm_strerror(status),
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_oracle_sample()
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_profile(args):
+    """Warm-up then --steps back-to-back steps; no flush, e2e or CPU leg."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2409_16659_gb300 import mlswlbm as B
+    p = workloads.film3_d2q9_params(NX, NY)
+    h0 = workloads.film3_d2q9_heights(NX, NY).astype(np.float32)
+    with B.Solver(p, h0, stream=torch.cuda.current_stream()) as s:
+        s.step(args.warmup)
+        s.step(args.steps)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_run": True, "launches": s.launch_count(),
+                          "status": B.mlswlbm_strerror(s.status())}), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="own", choices=["own", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="only warm-up + --steps back-to-back steps (for ncu captures)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.profile:
+        return run_profile(args)
+    return run_own(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,205 @@
+/*
+ * mlswlbm.h -- C ABI of the GB300 (sm_103a) multilayer shallow-water lattice
+ * Boltzmann solver for the n-layer thin-film equation (Richter, Malgaretti &
+ * Harting, "Modeling of thin liquid films with arbitrary many layers").
+ *
+ * One time step, for every lattice cell and liquid layer i = 1..n:
+ *   - moments h_i = sum_k f_ki, h_i U_i = sum_k c_k f_ki        (section LBM)
+ *   - interfaces z_i = sum_{j<=i} h_j, their lattice gradient and Laplacian
+ *   - Laplace pressure Lambda_i (Eq. Laplace_pressure) with the wetting
+ *     potential phi_k (Eq. wetting_potential) and disjoining pressure Pi_i
+ *     (Eq. disjoining_pressure); p_i - p_atm = sum_{j>=i} (Lambda_j + Pi_j)
+ *   - friction 2 mu_i h_i a_i from the velocity boundary conditions
+ *     (Eqs. u_ansatz, no_slip, flux, viscous_boundary, friction_force)
+ *   - force F_i = -h_i grad p_i + 2 mu_i h_i a_i (Eq. force)
+ *   - BGK collision with forcing and streaming (Eqs. BGK,
+ *     equilibrium_distribution) on a D1Q3 or D2Q9 lattice, periodic.
+ *
+ * Conventions for every entry point:
+ *   - Return value: MLSW_OK (0) or a negative MLSW_ERR_* code; no exception
+ *     or signal crosses the ABI. mlswlbm_strerror() names the code.
+ *   - Host arrays are owned by the caller and copied; the library never
+ *     keeps a caller pointer. Device memory of a handle is owned by the
+ *     handle and released by mlswlbm_destroy().
+ *   - All device work of a handle runs on the CUDA stream bound at create
+ *     (a cudaStream_t passed as void*, NULL = legacy default stream), so a
+ *     PyTorch stream's cuda_stream can be used. Entry points that return
+ *     host data synchronise that stream; the others are asynchronous.
+ *   - A handle is used by one host thread at a time.
+ *   - Layouts (row-major, x fastest, all FP32):
+ *       heights      h[i][y][x],          i = 0..n-1 (layer i+1)
+ *       populations  f[i][k][y][x],       k = lattice direction, paper order:
+ *         D1Q3: c = 0, +1, -1;
+ *         D2Q9: c = (0,0),(1,0),(1,1),(0,1),(-1,1),(-1,0),(-1,-1),(0,-1),(1,-1).
+ *     A state is stored post-streaming: f[i][k] at cell x arrived from x - c_k.
+ *   - Inside a handle the rest population of layer i is stored shifted by a
+ *     per-layer constant H_i (f_0 - H_i; H_i = mid-range of the layer in
+ *     h_init), which keeps the long-wave height differences representable
+ *     in FP32. mlswlbm_get_state / mlswlbm_set_state convert to and from the
+ *     true populations; mlswlbm_save_state / mlswlbm_load_state move the
+ *     internal representation unchanged (bit-exact checkpoints).
+ */
+#ifndef MLSWLBM_H
+#define MLSWLBM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MLSW_MAX_LAYERS 5
+#define MLSW_D1Q3 1
+#define MLSW_D2Q9 2
+
+/* flags */
+#define MLSW_FLAG_SKIP_STABILITY_CHECK 1
+
+/* return codes */
+#define MLSW_OK 0
+#define MLSW_ERR_ARG (-1)         /* invalid argument or parameter             */
+#define MLSW_ERR_NOMEM (-2)       /* device or host allocation failed          */
+#define MLSW_ERR_CUDA (-3)        /* a CUDA call failed                        */
+#define MLSW_ERR_NONFINITE (-4)   /* a kernel saw h <= 0 or a non-finite value */
+#define MLSW_ERR_UNSTABLE (-5)    /* explicit friction update not contractive  */
+#define MLSW_ERR_TIMEOUT (-6)     /* a bounded device wait ran out             */
+#define MLSW_ERR_UNSUPPORTED (-7) /* no kernel for this configuration          */
+
+/*
+ * Problem statement (section Model). Index conventions:
+ *   gamma[i-1]      gamma_{i,i+1}, tension of the interface above layer i,
+ *                   i = 1..n (layer n+1 is the gas).
+ *   spread[i][k-1]  spreading coefficient S_{ik} of Eq. (spreading_parameters),
+ *                   i = 0..n-1 (0 = substrate), k = 1..n-i; other entries
+ *                   are ignored.
+ *   mu[i-1]         viscosity mu_i > 0.
+ *   beta[i-1]       slip length beta_i >= 0 of Eq. (no_slip): beta_1 at the
+ *                   substrate, beta_{i>1} at the interface below layer i.
+ *   wet_n, wet_m    exponents of Eq. (wetting_potential), wet_n > wet_m >= 1.
+ *   hstar           precursor thickness h* > 0.
+ *   tau             BGK relaxation time of Eq. (BGK), tau > 1/2 (paper: 1).
+ *   nx, ny          periodic lattice size; D1Q3 needs ny == 1.
+ * The arithmetic is FP32 on the device; these doubles are rounded once.
+ */
+typedef struct mlsw_params {
+  int n_layers; /* 1..MLSW_MAX_LAYERS */
+  int lattice;  /* MLSW_D1Q3 or MLSW_D2Q9 */
+  int nx, ny;
+  double tau;
+  double gamma[MLSW_MAX_LAYERS];
+  double spread[MLSW_MAX_LAYERS][MLSW_MAX_LAYERS];
+  double mu[MLSW_MAX_LAYERS];
+  double beta[MLSW_MAX_LAYERS];
+  int wet_n, wet_m;
+  double hstar;
+  int flags; /* MLSW_FLAG_* */
+} mlsw_params;
+
+typedef struct mlsw_handle mlsw_handle;
+
+/*
+ * Fills p->spread (Eq. spreading_parameters) and p->gamma from the full
+ * tension table gamma_full[a * (n+2) + b] = gamma_{a,b}, a, b = 0..n+1
+ * (0 = substrate, n+1 = gas). Host only. Sets p->n_layers = n_layers.
+ * Errors: MLSW_ERR_ARG for a NULL pointer or n outside 1..MLSW_MAX_LAYERS.
+ */
+int mlswlbm_spreading_from_tensions(int n_layers, const double* gamma_full,
+                                    mlsw_params* p);
+
+/* Validates p without touching the GPU. MLSW_OK or MLSW_ERR_ARG. */
+int mlswlbm_check_params(const mlsw_params* p);
+
+/*
+ * Creates a solver: validates p, allocates two population buffers of
+ * n*Q*nx*ny floats plus small scratch on the current CUDA device, uploads
+ * h_init (host, [n][ny][nx], every value finite and > 0) and sets
+ * f = f_eq(h_init, U = 0) (Eq. equilibrium_distribution), i.e. the rest
+ * population carries h and the moving ones are zero.
+ * Unless p->flags has MLSW_FLAG_SKIP_STABILITY_CHECK, the explicit update of
+ * a uniform flux, J <- (1 + K) J with the friction matrix K of
+ * Eq. (friction_force), must be contractive at the per-layer minimum, mean
+ * and maximum of h_init and with every layer at h*; otherwise
+ * MLSW_ERR_UNSTABLE. stream: cudaStream_t or NULL.
+ * On failure *out is set to NULL and nothing is leaked.
+ */
+int mlswlbm_create(const mlsw_params* p, const float* h_init, void* stream,
+                   mlsw_handle** out);
+
+/* Enqueues nsteps >= 0 time steps (one fused kernel launch per step) on the
+ * handle's stream; asynchronous. MLSW_ERR_ARG for a NULL handle or
+ * nsteps < 0; MLSW_ERR_CUDA if a launch fails. */
+int mlswlbm_step(mlsw_handle* h, long nsteps);
+
+/* Heights h_i = sum_k f_ki into out (host, n*nx*ny floats). Synchronises.
+ * Returns MLSW_ERR_NONFINITE if any step since create or the last status
+ * query flagged h <= 0 or a non-finite value (out is still written). */
+int mlswlbm_get_heights(mlsw_handle* h, float* out);
+
+/* Same into device memory dev_out (n*nx*ny floats, caller-owned, on the
+ * handle's device); asynchronous, no status check. */
+int mlswlbm_get_heights_device(mlsw_handle* h, float* dev_out);
+
+/* Restarts from heights (host, [n][ny][nx]): f = f_eq(h, U = 0). The
+ * values are checked on the device: a value <= 0 or non-finite is reported
+ * as MLSW_ERR_NONFINITE by the next status query (mlswlbm_status,
+ * mlswlbm_get_heights, mlswlbm_get_diagnostics). The shift H_i of create is
+ * kept. Asynchronous on the handle's stream; h_in must stay valid until the
+ * stream reaches the copy (pageable memory is copied before return). */
+int mlswlbm_set_heights(mlsw_handle* h, const float* h_in);
+
+/* True population state (host, n*Q*nx*ny floats, layout above): copy out
+ * (synchronises) and copy in. The copy out rounds f_0 = H_i + (f_0 - H_i)
+ * to FP32, so a get/set round trip is not bit-exact; use save/load for
+ * that. */
+int mlswlbm_get_state(mlsw_handle* h, float* f_out);
+int mlswlbm_set_state(mlsw_handle* h, const float* f_in);
+
+/* Internal representation, unchanged: H_out / H_in = the n shifts H_i,
+ * g_out / g_in = n*Q*nx*ny floats laid out like f with the rest planes
+ * holding f_0 - H_i. Save then load resumes bit-exactly. Both synchronise.
+ * MLSW_ERR_ARG for NULL pointers or a non-finite shift. */
+int mlswlbm_save_state(mlsw_handle* h, float* H_out, float* g_out);
+int mlswlbm_load_state(mlsw_handle* h, const float* H_in, const float* g_in);
+
+/*
+ * Diagnostics of the current state, reduced on the device in double:
+ *   mass[i]   = sum_x h_i(x)                                (n doubles)
+ *   *kinetic  = sum_{i,x} |J_i(x)|^2 / (2 h_i(x))
+ *   *hmin     = min_{i,x} h_i(x)
+ * Any output pointer may be NULL. Synchronises. Returns MLSW_ERR_NONFINITE
+ * as mlswlbm_get_heights does.
+ */
+int mlswlbm_get_diagnostics(mlsw_handle* h, double* mass, double* kinetic,
+                            double* hmin);
+
+/* Synchronises and returns MLSW_OK or MLSW_ERR_NONFINITE (a kernel saw
+ * h <= 0 or a non-finite value since create or the last call); clears it. */
+int mlswlbm_status(mlsw_handle* h);
+
+/* Binds another stream to the handle (cudaStream_t or NULL). The caller
+ * orders work already queued on the old stream. */
+int mlswlbm_set_stream(mlsw_handle* h, void* stream);
+
+/* Number of GPU kernel launches this handle has issued since create. */
+long mlswlbm_launch_count(const mlsw_handle* h);
+
+/* Frees the handle and its device memory; NULL is accepted. Synchronises. */
+void mlswlbm_destroy(mlsw_handle* h);
+
+/* Static string for a return code; never NULL. */
+const char* mlswlbm_strerror(int code);
+
+/*
+ * Per-cell friction 2 mu_i h_i a_i (Eq. friction_force) for ncell
+ * independent cells, on the device. h, Jx, Jy, Rx, Ry: device pointers of
+ * n*ncell floats, layout [i][cell]; Jy/Ry may be NULL (one component).
+ * Only n_layers, mu and beta of p are used. Runs the same device routine
+ * the step kernels use; asynchronous on stream. Allocates nothing.
+ * Errors: MLSW_ERR_ARG (bad p or pointers), MLSW_ERR_CUDA (launch).
+ */
+int mlswlbm_friction_eval(const mlsw_params* p, long ncell, const float* h,
+                          const float* Jx, const float* Jy, float* Rx,
+                          float* Ry, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MLSWLBM_H */

@@ -1,0 +1,451 @@
+// mlswlbm.cu -- host side of the C ABI declared in include/mlswlbm.h:
+// parameter validation, spreading coefficients, the create-time stability
+// check, device buffers and the entry points.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "../../include/mlswlbm.h"
+#include "kernels.h"
+#include "physics.cuh"
+
+using mlsw::KParams;
+
+struct mlsw_handle {
+  mlsw_params p;
+  KParams kp;
+  int Q;
+  long ncell;
+  size_t flen;        // floats per population buffer
+  float* f[2];
+  int cur;            // index of the buffer holding the current state
+  float* hbuf;        // n * ncell heights (upload / read-out)
+  int* status;        // device flag, OR of kernel error bits
+  double* partials;   // diagnostics partials
+  double* dout;       // diagnostics result, n + 2 doubles
+  int nblk_diag;
+  cudaStream_t stream;
+  long launches;
+  mlsw::KShift sh;    // rest-population shift H_i (also in kp.H)
+};
+
+namespace {
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+int Qof(int lattice) { return lattice == MLSW_D1Q3 ? 3 : 9; }
+
+// ---------------------------------------------------------------------------
+// Explicit-update stability of a uniform flux (derived, not in the paper).
+// With tau = 1 the post-collision flux of a uniform state is J + K J, so the
+// update is contractive when the spectral radius of I + K is below 1. K is
+// built in double by the same shear-stress integration as the device
+// friction; rho(I + K) is bounded through ||(I + K)^m||^(1/m), m = 2^12.
+// ---------------------------------------------------------------------------
+bool friction_matrix(const mlsw_params& p, const double* h, double K[][MLSW_MAX_LAYERS]) {
+  const int n = p.n_layers;
+  double L[MLSW_MAX_LAYERS][MLSW_MAX_LAYERS];
+  for (int j = 0; j < n; ++j) {
+    double ub = 0.0;
+    for (int i = 0; i < n; ++i) {
+      const double s = (j > i) ? -h[j] : 0.0;
+      const double g = (i == j) ? 1.0 : 0.0;
+      const double mi = 1.0 / p.mu[i], bi = p.beta[i], hi = h[i];
+      ub += bi * mi * (s - g * (hi + 0.5 * bi));
+      L[i][j] = hi * ub + mi * hi * hi * (0.5 * s - g * hi / 3.0);
+      ub += mi * hi * (s - 0.5 * g * hi);
+    }
+  }
+  // X = L^-1 by Gauss-Jordan with partial pivoting
+  double A[MLSW_MAX_LAYERS][2 * MLSW_MAX_LAYERS];
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < 2 * n; ++c) A[r][c] = (c < n) ? L[r][c] : (c - n == r ? 1.0 : 0.0);
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(A[r][c]) > std::fabs(A[piv][c])) piv = r;
+    if (A[piv][c] == 0.0 || !std::isfinite(A[piv][c])) return false;
+    if (piv != c)
+      for (int q = 0; q < 2 * n; ++q) std::swap(A[c][q], A[piv][q]);
+    const double inv = 1.0 / A[c][c];
+    for (int q = 0; q < 2 * n; ++q) A[c][q] *= inv;
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      const double l = A[r][c];
+      for (int q = 0; q < 2 * n; ++q) A[r][q] -= l * A[c][q];
+    }
+  }
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < n; ++c) K[r][c] = h[r] * A[r][n + c];
+  return true;
+}
+
+double spectral_radius_I_plus_K(const mlsw_params& p, const double* h) {
+  const int n = p.n_layers;
+  double K[MLSW_MAX_LAYERS][MLSW_MAX_LAYERS];
+  if (!friction_matrix(p, h, K)) return INFINITY;
+  double A[MLSW_MAX_LAYERS][MLSW_MAX_LAYERS], B[MLSW_MAX_LAYERS][MLSW_MAX_LAYERS];
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < n; ++c) A[r][c] = K[r][c] + (r == c ? 1.0 : 0.0);
+  double logscale = 0.0;
+  const int squarings = 12;
+  for (int s = 0; s < squarings; ++s) {
+    double mx = 0.0;
+    for (int r = 0; r < n; ++r)
+      for (int c = 0; c < n; ++c) {
+        double acc = 0.0;
+        for (int q = 0; q < n; ++q) acc += A[r][q] * A[q][c];
+        B[r][c] = acc;
+        mx = std::fmax(mx, std::fabs(acc));
+      }
+    if (!(mx > 0.0)) return 0.0;
+    if (!std::isfinite(mx)) return INFINITY;
+    logscale = 2.0 * logscale + std::log(mx);
+    for (int r = 0; r < n; ++r)
+      for (int c = 0; c < n; ++c) A[r][c] = B[r][c] / mx;
+  }
+  double fro = 0.0;
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < n; ++c) fro += A[r][c] * A[r][c];
+  return std::exp((logscale + 0.5 * std::log(fro)) / std::ldexp(1.0, squarings));
+}
+
+KParams make_kparams(const mlsw_params& p) {
+  KParams k;
+  std::memset(&k, 0, sizeof(k));
+  k.n = p.n_layers;
+  k.nx = p.nx;
+  k.ny = p.ny;
+  k.omega = (float)(1.0 / p.tau);
+  for (int i = 0; i < p.n_layers; ++i) {
+    k.gamma[i] = (float)p.gamma[i];
+    k.mu_inv[i] = (float)(1.0 / p.mu[i]);
+    k.beta[i] = (float)p.beta[i];
+    for (int kk = 1; kk <= p.n_layers - i; ++kk) k.S[i][kk - 1] = (float)p.spread[i][kk - 1];
+  }
+  k.hstar = (float)p.hstar;
+  k.nw = p.wet_n;
+  k.mw = p.wet_m;
+  k.c_phi = (float)(1.0 / (p.wet_n - p.wet_m));
+  k.c_dphi = (float)((double)p.wet_n * p.wet_m / (p.wet_n - p.wet_m));
+  return k;
+}
+
+int check_heights(const mlsw_params& p, const float* h) {
+  const long total = (long)p.n_layers * p.nx * p.ny;
+  for (long t = 0; t < total; ++t)
+    if (!(std::isfinite(h[t]) && h[t] > 0.f)) return MLSW_ERR_ARG;
+  return MLSW_OK;
+}
+
+#define CU(call)                                     \
+  do {                                               \
+    if ((call) != cudaSuccess) return MLSW_ERR_CUDA; \
+  } while (0)
+
+void set_shift(mlsw_handle* h, const float* H) {
+  for (int i = 0; i < mlsw::kMaxLayers; ++i) {
+    const float v = (i < h->p.n_layers) ? H[i] : 0.f;
+    h->sh.H[i] = v;
+    h->kp.H[i] = v;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mlswlbm_strerror(int code) {
+  switch (code) {
+    case MLSW_OK: return "ok";
+    case MLSW_ERR_ARG: return "invalid argument";
+    case MLSW_ERR_NOMEM: return "out of memory";
+    case MLSW_ERR_CUDA: return "CUDA call failed";
+    case MLSW_ERR_NONFINITE: return "non-finite value or non-positive layer height";
+    case MLSW_ERR_UNSTABLE: return "explicit friction update not contractive";
+    case MLSW_ERR_TIMEOUT: return "device wait timed out";
+    case MLSW_ERR_UNSUPPORTED: return "unsupported configuration";
+    default: return "unknown error";
+  }
+}
+
+int mlswlbm_spreading_from_tensions(int n, const double* g, mlsw_params* p) {
+  if (!g || !p || n < 1 || n > MLSW_MAX_LAYERS) return MLSW_ERR_ARG;
+  const int G = n + 2;
+  p->n_layers = n;
+  for (int i = 0; i < MLSW_MAX_LAYERS; ++i)
+    for (int k = 0; k < MLSW_MAX_LAYERS; ++k) p->spread[i][k] = 0.0;
+  // Eq. (spreading_parameters)
+  for (int i = 0; i < n; ++i)
+    for (int k = 1; k <= n - i; ++k) {
+      double s;
+      if (k == 1)
+        s = g[i * G + i + 2] - g[i * G + i + 1] - g[(i + 1) * G + i + 2];
+      else
+        s = g[i * G + i + k + 1] + g[(i + 1) * G + i + k] - g[i * G + i + k] -
+            g[(i + 1) * G + i + k + 1];
+      p->spread[i][k - 1] = s;
+    }
+  for (int i = 1; i <= n; ++i) p->gamma[i - 1] = g[i * G + i + 1];
+  return MLSW_OK;
+}
+
+int mlswlbm_check_params(const mlsw_params* p) {
+  if (!p) return MLSW_ERR_ARG;
+  const int n = p->n_layers;
+  if (n < 1 || n > MLSW_MAX_LAYERS) return MLSW_ERR_ARG;
+  if (p->lattice != MLSW_D1Q3 && p->lattice != MLSW_D2Q9) return MLSW_ERR_ARG;
+  if (p->nx < 1 || p->ny < 1) return MLSW_ERR_ARG;
+  if (p->lattice == MLSW_D1Q3 && p->ny != 1) return MLSW_ERR_ARG;
+  const double cells = (double)p->nx * p->ny * n * Qof(p->lattice);
+  if (cells > 4.0e9) return MLSW_ERR_ARG;  // 32-bit tile indexing limit, 16 GB per buffer
+  if (!std::isfinite(p->tau) || !(p->tau > 0.5)) return MLSW_ERR_ARG;
+  if (!finite_pos(p->hstar)) return MLSW_ERR_ARG;
+  if (p->wet_m < 1 || p->wet_n <= p->wet_m || p->wet_n > 64) return MLSW_ERR_ARG;
+  for (int i = 0; i < n; ++i) {
+    if (!finite_pos(p->mu[i])) return MLSW_ERR_ARG;
+    if (!std::isfinite(p->beta[i]) || p->beta[i] < 0.0) return MLSW_ERR_ARG;
+    if (!std::isfinite(p->gamma[i])) return MLSW_ERR_ARG;
+    for (int k = 1; k <= n - i; ++k)
+      if (!std::isfinite(p->spread[i][k - 1])) return MLSW_ERR_ARG;
+  }
+  return MLSW_OK;
+}
+
+void mlswlbm_destroy(mlsw_handle* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  cudaFree(h->f[0]);
+  cudaFree(h->f[1]);
+  cudaFree(h->hbuf);
+  cudaFree(h->status);
+  cudaFree(h->partials);
+  cudaFree(h->dout);
+  delete h;
+}
+
+int mlswlbm_create(const mlsw_params* p, const float* h_init, void* stream, mlsw_handle** out) {
+  if (!out) return MLSW_ERR_ARG;
+  *out = nullptr;
+  int rc = mlswlbm_check_params(p);
+  if (rc != MLSW_OK) return rc;
+  if (!h_init) return MLSW_ERR_ARG;
+  rc = check_heights(*p, h_init);
+  if (rc != MLSW_OK) return rc;
+  const int n = p->n_layers;
+  const long ncell = (long)p->nx * p->ny;
+
+  double hmin[MLSW_MAX_LAYERS], hmax[MLSW_MAX_LAYERS], hmean[MLSW_MAX_LAYERS],
+      hst[MLSW_MAX_LAYERS];
+  float shift[MLSW_MAX_LAYERS];
+  for (int i = 0; i < n; ++i) {
+    double mn = INFINITY, mx = -INFINITY, sum = 0.0;
+    for (long c = 0; c < ncell; ++c) {
+      const double v = h_init[(long)i * ncell + c];
+      mn = std::fmin(mn, v);
+      mx = std::fmax(mx, v);
+      sum += v;
+    }
+    hmin[i] = mn;
+    hmax[i] = mx;
+    hmean[i] = sum / (double)ncell;
+    hst[i] = p->hstar;
+    // mid-range: independent of the order of the cells (so a translated
+    // field gets the same shift) and within the field's range
+    shift[i] = (float)(0.5 * (mn + mx));
+  }
+  if (!(p->flags & MLSW_FLAG_SKIP_STABILITY_CHECK)) {
+    const double* states[4] = {hst, hmin, hmean, hmax};
+    for (const double* s : states)
+      if (!(spectral_radius_I_plus_K(*p, s) < 1.0)) return MLSW_ERR_UNSTABLE;
+  }
+
+  mlsw_handle* h = new (std::nothrow) mlsw_handle;
+  if (!h) return MLSW_ERR_NOMEM;
+  std::memset(h, 0, sizeof(*h));
+  h->p = *p;
+  h->kp = make_kparams(*p);
+  h->Q = Qof(p->lattice);
+  h->ncell = ncell;
+  h->flen = (size_t)n * h->Q * ncell;
+  h->stream = (cudaStream_t)stream;
+  set_shift(h, shift);
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    delete h;
+    return MLSW_ERR_CUDA;
+  }
+  h->nblk_diag = 2 * (sms > 0 ? sms : 1);
+  bool ok = cudaMalloc(&h->f[0], h->flen * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&h->f[1], h->flen * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&h->hbuf, (size_t)n * ncell * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&h->status, sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&h->partials, (size_t)h->nblk_diag * (n + 2) * sizeof(double)) ==
+                cudaSuccess &&
+            cudaMalloc(&h->dout, (size_t)(n + 2) * sizeof(double)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    mlswlbm_destroy(h);
+    return MLSW_ERR_NOMEM;
+  }
+  if (cudaMemsetAsync(h->status, 0, sizeof(int), h->stream) != cudaSuccess) {
+    mlswlbm_destroy(h);
+    return MLSW_ERR_CUDA;
+  }
+  rc = mlswlbm_set_heights(h, h_init);
+  if (rc == MLSW_OK && cudaStreamSynchronize(h->stream) != cudaSuccess) rc = MLSW_ERR_CUDA;
+  if (rc != MLSW_OK) {
+    mlswlbm_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return MLSW_OK;
+}
+
+int mlswlbm_set_heights(mlsw_handle* h, const float* h_in) {
+  if (!h || !h_in) return MLSW_ERR_ARG;
+  const size_t bytes = (size_t)h->p.n_layers * h->ncell * sizeof(float);
+  CU(cudaMemcpyAsync(h->hbuf, h_in, bytes, cudaMemcpyHostToDevice, h->stream));
+  CU(mlsw::launch_init(h->Q, h->p.n_layers, h->ncell, h->hbuf, h->f[h->cur], h->sh,
+                       h->status, h->stream));
+  h->launches += 1;
+  return MLSW_OK;
+}
+
+int mlswlbm_step(mlsw_handle* h, long nsteps) {
+  if (!h || nsteps < 0) return MLSW_ERR_ARG;
+  for (long s = 0; s < nsteps; ++s) {
+    const float* fin = h->f[h->cur];
+    float* fout = h->f[h->cur ^ 1];
+    CU(mlsw::launch_step(h->p.lattice, fin, fout, h->kp, h->status, h->stream));
+    h->cur ^= 1;
+    h->launches += 1;
+  }
+  return MLSW_OK;
+}
+
+int mlswlbm_status(mlsw_handle* h) {
+  if (!h) return MLSW_ERR_ARG;
+  int flag = 0;
+  CU(cudaMemcpyAsync(&flag, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  if (flag) {
+    CU(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
+    return MLSW_ERR_NONFINITE;
+  }
+  return MLSW_OK;
+}
+
+int mlswlbm_get_heights_device(mlsw_handle* h, float* dev_out) {
+  if (!h || !dev_out) return MLSW_ERR_ARG;
+  CU(mlsw::launch_heights(h->Q, h->p.n_layers, h->ncell, h->f[h->cur], h->sh, dev_out,
+                          h->stream));
+  h->launches += 1;
+  return MLSW_OK;
+}
+
+int mlswlbm_get_heights(mlsw_handle* h, float* out) {
+  if (!h || !out) return MLSW_ERR_ARG;
+  int rc = mlswlbm_get_heights_device(h, h->hbuf);
+  if (rc != MLSW_OK) return rc;
+  const size_t bytes = (size_t)h->p.n_layers * h->ncell * sizeof(float);
+  CU(cudaMemcpyAsync(out, h->hbuf, bytes, cudaMemcpyDeviceToHost, h->stream));
+  return mlswlbm_status(h);
+}
+
+int mlswlbm_get_state(mlsw_handle* h, float* f_out) {
+  if (!h || !f_out) return MLSW_ERR_ARG;
+  const int n = h->p.n_layers;
+  const size_t plane = (size_t)h->ncell;
+  // rest planes H_i + g_0 into the height buffer, all planes raw to the host,
+  // then the rest planes over their raw copies
+  CU(mlsw::launch_rest_planes(h->Q, n, h->ncell, h->f[h->cur], h->sh, h->hbuf, h->stream));
+  h->launches += 1;
+  CU(cudaMemcpyAsync(f_out, h->f[h->cur], h->flen * sizeof(float), cudaMemcpyDeviceToHost,
+                     h->stream));
+  for (int i = 0; i < n; ++i)
+    CU(cudaMemcpyAsync(f_out + (size_t)i * h->Q * plane, h->hbuf + (size_t)i * plane,
+                       plane * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  return MLSW_OK;
+}
+
+int mlswlbm_set_state(mlsw_handle* h, const float* f_in) {
+  if (!h || !f_in) return MLSW_ERR_ARG;
+  CU(cudaMemcpyAsync(h->f[h->cur], f_in, h->flen * sizeof(float), cudaMemcpyHostToDevice,
+                     h->stream));
+  CU(mlsw::launch_shift(h->Q, h->p.n_layers, h->ncell, h->f[h->cur], h->sh, -1.f, h->stream));
+  h->launches += 1;
+  CU(cudaStreamSynchronize(h->stream));
+  return MLSW_OK;
+}
+
+int mlswlbm_save_state(mlsw_handle* h, float* H_out, float* g_out) {
+  if (!h || !H_out || !g_out) return MLSW_ERR_ARG;
+  for (int i = 0; i < h->p.n_layers; ++i) H_out[i] = h->sh.H[i];
+  CU(cudaMemcpyAsync(g_out, h->f[h->cur], h->flen * sizeof(float), cudaMemcpyDeviceToHost,
+                     h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  return MLSW_OK;
+}
+
+int mlswlbm_load_state(mlsw_handle* h, const float* H_in, const float* g_in) {
+  if (!h || !H_in || !g_in) return MLSW_ERR_ARG;
+  for (int i = 0; i < h->p.n_layers; ++i)
+    if (!std::isfinite(H_in[i])) return MLSW_ERR_ARG;
+  CU(cudaStreamSynchronize(h->stream));
+  set_shift(h, H_in);
+  CU(cudaMemcpyAsync(h->f[h->cur], g_in, h->flen * sizeof(float), cudaMemcpyHostToDevice,
+                     h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  return MLSW_OK;
+}
+
+int mlswlbm_get_diagnostics(mlsw_handle* h, double* mass, double* kinetic, double* hmin) {
+  if (!h) return MLSW_ERR_ARG;
+  const int n = h->p.n_layers;
+  CU(mlsw::launch_diagnostics(h->p.lattice, n, h->ncell, h->f[h->cur], h->sh, h->partials,
+                              h->nblk_diag, h->dout, h->stream));
+  h->launches += 2;
+  double res[MLSW_MAX_LAYERS + 2];
+  CU(cudaMemcpyAsync(res, h->dout, (size_t)(n + 2) * sizeof(double), cudaMemcpyDeviceToHost,
+                     h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  if (mass)
+    for (int i = 0; i < n; ++i) mass[i] = res[i];
+  if (kinetic) *kinetic = res[n];
+  if (hmin) *hmin = res[n + 1];
+  return mlswlbm_status(h);
+}
+
+int mlswlbm_set_stream(mlsw_handle* h, void* stream) {
+  if (!h) return MLSW_ERR_ARG;
+  h->stream = (cudaStream_t)stream;
+  return MLSW_OK;
+}
+
+long mlswlbm_launch_count(const mlsw_handle* h) { return h ? h->launches : -1; }
+
+int mlswlbm_friction_eval(const mlsw_params* p, long ncell, const float* hh, const float* Jx,
+                          const float* Jy, float* Rx, float* Ry, void* stream) {
+  if (!p || ncell < 0 || !hh || !Jx || !Rx) return MLSW_ERR_ARG;
+  const int n = p->n_layers;
+  if (n < 1 || n > MLSW_MAX_LAYERS) return MLSW_ERR_ARG;
+  for (int i = 0; i < n; ++i)
+    if (!finite_pos(p->mu[i]) || !std::isfinite(p->beta[i]) || p->beta[i] < 0.0)
+      return MLSW_ERR_ARG;
+  if (ncell == 0) return MLSW_OK;
+  KParams k;
+  std::memset(&k, 0, sizeof(k));
+  k.n = n;
+  for (int i = 0; i < n; ++i) {
+    k.mu_inv[i] = (float)(1.0 / p->mu[i]);
+    k.beta[i] = (float)p->beta[i];
+  }
+  CU(mlsw::launch_friction_eval(k, ncell, hh, Jx, Jy, Rx, Ry, (cudaStream_t)stream));
+  return MLSW_OK;
+}
+
+}  // extern "C"

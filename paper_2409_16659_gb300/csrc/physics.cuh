@@ -1,0 +1,221 @@
+// physics.cuh -- per-cell device routines of the multilayer shallow-water
+// LBM step (FP32): lattice tables, layer pressures, friction coupling,
+// equilibrium/collision. Used by the step kernels and by
+// mlswlbm_friction_eval.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace mlsw {
+
+constexpr int kMaxLayers = 5;
+
+// Kernel-side copy of the problem statement, rounded to FP32 once.
+//
+// Shifted rest population: the device stores g_0 = f_0 - H_i for the rest
+// population of layer i (H_i a per-layer constant near the film thickness)
+// and g_k = f_k otherwise. Moments are then formed as deviations
+// dh_i = sum_k g_k (h_i = H_i + dh_i), so the interface stencils work on
+// O(1e-3) numbers instead of O(1) ones. In FP32 the long-wave curvature of
+// an O(1) height field is comparable to its rounding (ulp(1) = 1.2e-7), so
+// storing f_0 itself loses the capillary signal; the shift keeps ~1e-10.
+// The arithmetic of the scheme is unchanged: only the representation of
+// f_0 moves by a constant.
+struct KParams {
+  int n;
+  int nx, ny;
+  float omega;                       // 1 / tau
+  float gamma[kMaxLayers];           // gamma_{i,i+1}
+  float S[kMaxLayers][kMaxLayers];   // S[l][k-1] = S_{lk}
+  float mu_inv[kMaxLayers];          // 1 / mu_i
+  float beta[kMaxLayers];            // beta_i
+  float hstar;
+  int nw, mw;
+  float c_phi;                       // 1 / (nw - mw)
+  float c_dphi;                      // nw mw / (nw - mw)
+  float H[kMaxLayers];               // rest-population shift of each layer
+};
+
+// ---------------------------------------------------------------------------
+// lattices (section LBM): c_0 = 0, then the paper's order
+// ---------------------------------------------------------------------------
+template <int LAT> struct Lattice;
+
+template <> struct Lattice<1> {  // D1Q3
+  static constexpr int Q = 3;
+  __host__ __device__ static constexpr int cx(int k) { return k == 1 ? 1 : (k == 2 ? -1 : 0); }
+  __host__ __device__ static constexpr int cy(int) { return 0; }
+  __host__ __device__ static constexpr float w(int k) { return k == 0 ? 2.f / 3.f : 1.f / 6.f; }
+};
+
+template <> struct Lattice<2> {  // D2Q9, counter-clockwise from +x
+  static constexpr int Q = 9;
+  __host__ __device__ static constexpr int cx(int k) {
+    return (k == 1 || k == 2 || k == 8) ? 1 : ((k == 4 || k == 5 || k == 6) ? -1 : 0);
+  }
+  __host__ __device__ static constexpr int cy(int k) {
+    return (k == 2 || k == 3 || k == 4) ? 1 : ((k == 6 || k == 7 || k == 8) ? -1 : 0);
+  }
+  __host__ __device__ static constexpr float w(int k) {
+    return k == 0 ? 4.f / 9.f : ((k & 1) ? 1.f / 9.f : 1.f / 36.f);
+  }
+};
+
+__device__ __forceinline__ float ipow(float r, int e) {
+  float a = 1.f;
+  for (int i = 0; i < e; ++i) a *= r;
+  return a;
+}
+
+// ---------------------------------------------------------------------------
+// Layer pressures p_i - p_atm at one cell (Eqs. Laplace_pressure,
+// disjoining_pressure; p_i = sum_{j>=i} (Lambda_j + Pi_j)).
+// Every interface pair (l, m = l + k), 0 <= l < m <= N, enters once:
+// thickness d = z_m - z_l = h_{l+1} + ... + h_m (summed from h, no
+// cancellation), E = S_lk phi'_k(d) (1 + |grad z_l|^2 / 2) is subtracted from
+// Pi_l and added to Pi_m, and S_lk phi_k(d) raises the tension of interface
+// l. l = 0 is the flat substrate (grad z_0 = 0, no pressure of its own).
+// ---------------------------------------------------------------------------
+template <int N>
+__device__ __forceinline__ void layer_pressures(const KParams& P, const float (&h)[N],
+                                                const float (&gx)[N], const float (&gy)[N],
+                                                const float (&lz)[N], float (&p)[N]) {
+  float ten[N], pi[N], sg[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    ten[i] = P.gamma[i];
+    pi[i] = 0.f;
+    sg[i] = 1.f + 0.5f * (gx[i] * gx[i] + gy[i] * gy[i]);
+  }
+#pragma unroll
+  for (int l = 0; l < N; ++l) {
+    const float sgl = (l == 0) ? 1.f : sg[l > 0 ? l - 1 : 0];
+    float d = 0.f;
+#pragma unroll
+    for (int m = l + 1; m <= N; ++m) {
+      d += h[m - 1];
+      const int k = m - l;
+      const float s = P.S[l][k - 1];
+      if (s != 0.f) {
+        const float inv_d = 1.f / d;
+        const float r = (float)k * P.hstar * inv_d;
+        const float rm = ipow(r, P.mw), rn = ipow(r, P.nw);
+        const float phi = ((float)P.nw * rm - (float)P.mw * rn) * P.c_phi;
+        const float dphi = P.c_dphi * (rn - rm) * inv_d;
+        const float e = s * dphi * sgl;
+        if (l >= 1) {
+          ten[l > 0 ? l - 1 : 0] += s * phi;
+          pi[l > 0 ? l - 1 : 0] -= e;
+        }
+        pi[m - 1] += e;
+      }
+    }
+  }
+  float acc = 0.f;
+#pragma unroll
+  for (int i = N - 1; i >= 0; --i) {
+    acc += pi[i] - ten[i] * lz[i];
+    p[i] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Friction 2 mu_i h_i a_i (Eq. friction_force) by shear-stress integration.
+//
+// In Stokes layers with pressure gradient G_i, mu_i u'' = G_i. Integrating
+// the stress down from the stress-free top (Eq. viscous_boundary with
+// mu_{n+1} = 0) gives, in layer i, sigma(z) = G_i (z - z_i) - sum_{j>i} h_j G_j.
+// Integrating u = sigma / mu_i upward from the substrate, the slip condition
+// of Eq. (no_slip) -- the parabola of layer i continued a distance beta_i
+// below z_{i-1} meets u_{i-1}(z_{i-1}) -- adds the jump
+// (beta_i / mu_i) sigma_i(z_{i-1} - beta_i / 2). Integrating u over each
+// layer (Eq. flux) gives J = L G with an N x N matrix L built column by
+// column in O(N^2). Force balance of the thin-sheet equation,
+// 0 = -h_i G_i + 2 mu_i h_i a_i, then gives the friction R_i = h_i G_i with
+// G = L^-1 J: one factorisation, two right-hand sides (x and y).
+// L is not symmetric in general (the slip convention breaks reciprocity), so
+// the elimination pivots by rows.
+// ---------------------------------------------------------------------------
+template <int N>
+__device__ __forceinline__ void friction(const KParams& P, const float (&h)[N],
+                                         const float (&Jx)[N], const float (&Jy)[N],
+                                         float (&Rx)[N], float (&Ry)[N]) {
+  float L[N][N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    float ub = 0.f;  // velocity at the bottom of layer i for unit G_j
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const float s = (j > i) ? -h[j] : 0.f;  // stress at z_i
+      const float g = (i == j) ? 1.f : 0.f;
+      const float mi = P.mu_inv[i], bi = P.beta[i], hi = h[i];
+      ub += bi * mi * (s - g * (hi + 0.5f * bi));
+      L[i][j] = hi * ub + mi * hi * hi * (0.5f * s - g * (1.f / 3.f) * hi);
+      ub += mi * hi * (s - 0.5f * g * hi);
+    }
+  }
+  float bx[N], by[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    bx[i] = Jx[i];
+    by[i] = Jy[i];
+  }
+  float inv_piv[N];
+#pragma unroll
+  for (int c = 0; c < N; ++c) {
+    int piv = c;
+    float best = fabsf(L[c][c]);
+#pragma unroll
+    for (int r = c + 1; r < N; ++r) {
+      const float a = fabsf(L[r][c]);
+      if (a > best) {
+        best = a;
+        piv = r;
+      }
+    }
+#pragma unroll
+    for (int r = c + 1; r < N; ++r) {
+      if (piv == r) {
+#pragma unroll
+        for (int q = c; q < N; ++q) {
+          const float t = L[c][q];
+          L[c][q] = L[r][q];
+          L[r][q] = t;
+        }
+        float t = bx[c];
+        bx[c] = bx[r];
+        bx[r] = t;
+        t = by[c];
+        by[c] = by[r];
+        by[r] = t;
+      }
+    }
+    inv_piv[c] = 1.f / L[c][c];
+#pragma unroll
+    for (int r = c + 1; r < N; ++r) {
+      const float l = L[r][c] * inv_piv[c];
+#pragma unroll
+      for (int q = c + 1; q < N; ++q) L[r][q] -= l * L[c][q];
+      bx[r] -= l * bx[c];
+      by[r] -= l * by[c];
+    }
+  }
+#pragma unroll
+  for (int c = N - 1; c >= 0; --c) {
+    float sx = bx[c], sy = by[c];
+#pragma unroll
+    for (int q = c + 1; q < N; ++q) {
+      sx -= L[c][q] * bx[q];
+      sy -= L[c][q] * by[q];
+    }
+    bx[c] = sx * inv_piv[c];
+    by[c] = sy * inv_piv[c];
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    Rx[i] = h[i] * bx[i];
+    Ry[i] = h[i] * by[i];
+  }
+}
+
+}  // namespace mlsw

@@ -1,0 +1,356 @@
+"""Thin ctypes binding of the C ABI in include/mlswlbm.h (same names).
+
+Argument marshalling only: every step of the solver runs in the CUDA library
+libmlswlbm.so. Loading fails loudly if the library is missing; there is no
+CPU path.
+
+Parameter dicts (also accepted by the oracle) use the keys
+    n, lattice (1 = D1Q3, 2 = D2Q9), nx, ny, tau, gamma[n], S[i][k-1],
+    mu[n], beta[n], nw, mw, hstar (and optional flags).
+Host arrays are numpy float32 (or anything numpy can view as such);
+device arrays are torch CUDA tensors (float32, contiguous). PyTorch is used
+only for device memory and streams.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+MLSW_MAX_LAYERS = 5
+MLSW_D1Q3 = 1
+MLSW_D2Q9 = 2
+MLSW_FLAG_SKIP_STABILITY_CHECK = 1
+
+MLSW_OK = 0
+MLSW_ERR_ARG = -1
+MLSW_ERR_NOMEM = -2
+MLSW_ERR_CUDA = -3
+MLSW_ERR_NONFINITE = -4
+MLSW_ERR_UNSTABLE = -5
+MLSW_ERR_TIMEOUT = -6
+MLSW_ERR_UNSUPPORTED = -7
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libmlswlbm.so")
+
+
+class mlsw_params(ctypes.Structure):
+    _fields_ = [
+        ("n_layers", ctypes.c_int),
+        ("lattice", ctypes.c_int),
+        ("nx", ctypes.c_int),
+        ("ny", ctypes.c_int),
+        ("tau", ctypes.c_double),
+        ("gamma", ctypes.c_double * MLSW_MAX_LAYERS),
+        ("spread", (ctypes.c_double * MLSW_MAX_LAYERS) * MLSW_MAX_LAYERS),
+        ("mu", ctypes.c_double * MLSW_MAX_LAYERS),
+        ("beta", ctypes.c_double * MLSW_MAX_LAYERS),
+        ("wet_n", ctypes.c_int),
+        ("wet_m", ctypes.c_int),
+        ("hstar", ctypes.c_double),
+        ("flags", ctypes.c_int),
+    ]
+
+
+class MlswError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__("%s: %s (%d)" % (where, mlswlbm_strerror(code), code))
+
+
+_lib = None
+_P = ctypes.POINTER(mlsw_params)
+_H = ctypes.c_void_p
+_F = ctypes.POINTER(ctypes.c_float)
+_D = ctypes.POINTER(ctypes.c_double)
+
+EXPORTS = {
+    "mlswlbm_spreading_from_tensions": (ctypes.c_int, [ctypes.c_int, _D, _P]),
+    "mlswlbm_check_params": (ctypes.c_int, [_P]),
+    "mlswlbm_create": (ctypes.c_int, [_P, _F, ctypes.c_void_p, ctypes.POINTER(_H)]),
+    "mlswlbm_step": (ctypes.c_int, [_H, ctypes.c_long]),
+    "mlswlbm_get_heights": (ctypes.c_int, [_H, _F]),
+    "mlswlbm_get_heights_device": (ctypes.c_int, [_H, ctypes.c_void_p]),
+    "mlswlbm_set_heights": (ctypes.c_int, [_H, _F]),
+    "mlswlbm_get_state": (ctypes.c_int, [_H, _F]),
+    "mlswlbm_set_state": (ctypes.c_int, [_H, _F]),
+    "mlswlbm_save_state": (ctypes.c_int, [_H, _F, _F]),
+    "mlswlbm_load_state": (ctypes.c_int, [_H, _F, _F]),
+    "mlswlbm_get_diagnostics": (ctypes.c_int, [_H, _D, _D, _D]),
+    "mlswlbm_status": (ctypes.c_int, [_H]),
+    "mlswlbm_set_stream": (ctypes.c_int, [_H, ctypes.c_void_p]),
+    "mlswlbm_launch_count": (ctypes.c_long, [_H]),
+    "mlswlbm_destroy": (None, [_H]),
+    "mlswlbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "mlswlbm_friction_eval": (ctypes.c_int, [_P, ctypes.c_long, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p]),
+}
+
+
+def lib():
+    """Loads libmlswlbm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libmlswlbm.so is not built; run "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in EXPORTS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc, where):
+    if rc != MLSW_OK:
+        raise MlswError(rc, where)
+
+
+def mlswlbm_strerror(code):
+    return lib().mlswlbm_strerror(int(code)).decode()
+
+
+def make_params(p):
+    """dict -> mlsw_params (marshalling only)."""
+    s = mlsw_params()
+    n = int(p["n"])
+    if not 1 <= n <= MLSW_MAX_LAYERS:
+        raise ValueError("n must be in 1..%d" % MLSW_MAX_LAYERS)
+    s.n_layers = n
+    s.lattice = int(p.get("lattice", MLSW_D2Q9))
+    s.nx = int(p.get("nx", 1))
+    s.ny = int(p.get("ny", 1))
+    s.tau = float(p.get("tau", 1.0))
+    for i in range(n):
+        s.gamma[i] = float(p["gamma"][i])
+        s.mu[i] = float(p["mu"][i])
+        s.beta[i] = float(p["beta"][i])
+    S = p.get("S")
+    if S is not None:
+        for i in range(n):
+            for k in range(1, n - i + 1):
+                s.spread[i][k - 1] = float(S[i][k - 1])
+    s.wet_n = int(p["nw"])
+    s.wet_m = int(p["mw"])
+    s.hstar = float(p["hstar"])
+    s.flags = int(p.get("flags", 0))
+    return s
+
+
+def _host_f32(a, size=None):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if size is not None and a.size != size:
+        raise ValueError("expected %d floats, got %d" % (size, a.size))
+    return a
+
+
+def _fptr(a):
+    return a.ctypes.data_as(_F)
+
+
+def _dev_ptr(t, numel=None):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32
+            and t.is_contiguous()):
+        raise ValueError("expected a contiguous float32 CUDA tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError("expected %d elements, got %d" % (numel, t.numel()))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def mlswlbm_spreading_from_tensions(n, gamma_full, p=None):
+    """Returns (S rows, gamma list) for the (n+2)^2 tension table."""
+    s = make_params(p) if p is not None else mlsw_params()
+    g = np.ascontiguousarray(gamma_full, dtype=np.float64)
+    if g.size != (n + 2) ** 2:
+        raise ValueError("tension table must have (n+2)^2 entries")
+    _check(lib().mlswlbm_spreading_from_tensions(int(n), g.ctypes.data_as(_D),
+                                                 ctypes.byref(s)),
+           "mlswlbm_spreading_from_tensions")
+    S = [[s.spread[i][k - 1] for k in range(1, n - i + 1)] for i in range(n)]
+    return S, [s.gamma[i] for i in range(n)]
+
+
+def mlswlbm_check_params(p):
+    s = make_params(p)
+    return lib().mlswlbm_check_params(ctypes.byref(s))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)  # torch.cuda.Stream
+
+
+class Solver:
+    """Owns one mlsw_handle. Methods map 1:1 to the C entry points."""
+
+    def __init__(self, p, h_init, stream=None):
+        self.p = dict(p)
+        self.n = int(p["n"])
+        self.nx = int(p.get("nx", 1))
+        self.ny = int(p.get("ny", 1))
+        self.Q = 3 if int(p.get("lattice", 2)) == MLSW_D1Q3 else 9
+        self.ncell = self.nx * self.ny
+        self._params = make_params(p)
+        h = _host_f32(h_init, self.n * self.ncell)
+        self._h = _H()
+        _check(lib().mlswlbm_create(ctypes.byref(self._params), _fptr(h),
+                                    _stream_ptr(stream), ctypes.byref(self._h)),
+               "mlswlbm_create")
+
+    # -- lifecycle ---------------------------------------------------------
+    def close(self):
+        if self._h:
+            lib().mlswlbm_destroy(self._h)
+            self._h = _H()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- entry points --------------------------------------------------------
+    def step(self, nsteps=1):
+        _check(lib().mlswlbm_step(self._h, int(nsteps)), "mlswlbm_step")
+
+    def get_heights(self, out=None):
+        shape = (self.n, self.ny, self.nx)
+        if out is None:
+            out = np.empty(shape, dtype=np.float32)
+        rc = lib().mlswlbm_get_heights(self._h, _fptr(_checked_out(out, self.n * self.ncell)))
+        _check(rc, "mlswlbm_get_heights")
+        return out
+
+    def get_heights_device(self, dev_out):
+        _check(lib().mlswlbm_get_heights_device(self._h, _dev_ptr(dev_out, self.n * self.ncell)),
+               "mlswlbm_get_heights_device")
+        return dev_out
+
+    def set_heights(self, h):
+        a = _host_f32(h, self.n * self.ncell)
+        _check(lib().mlswlbm_set_heights(self._h, _fptr(a)), "mlswlbm_set_heights")
+
+    def get_state(self, out=None):
+        shape = (self.n, self.Q, self.ny, self.nx)
+        if out is None:
+            out = np.empty(shape, dtype=np.float32)
+        _check(lib().mlswlbm_get_state(self._h, _fptr(_checked_out(out, out.size))),
+               "mlswlbm_get_state")
+        return out
+
+    def set_state(self, f):
+        a = _host_f32(f, self.n * self.Q * self.ncell)
+        _check(lib().mlswlbm_set_state(self._h, _fptr(a)), "mlswlbm_set_state")
+
+    def save_state(self):
+        """(H, g): the internal representation (bit-exact checkpoint)."""
+        H = np.empty(self.n, dtype=np.float32)
+        g = np.empty((self.n, self.Q, self.ny, self.nx), dtype=np.float32)
+        _check(lib().mlswlbm_save_state(self._h, _fptr(H), _fptr(g)), "mlswlbm_save_state")
+        return H, g
+
+    def load_state(self, H, g):
+        Ha = _host_f32(H, self.n)
+        ga = _host_f32(g, self.n * self.Q * self.ncell)
+        _check(lib().mlswlbm_load_state(self._h, _fptr(Ha), _fptr(ga)), "mlswlbm_load_state")
+
+    def get_diagnostics(self):
+        mass = (ctypes.c_double * self.n)()
+        ke = ctypes.c_double()
+        hmin = ctypes.c_double()
+        rc = lib().mlswlbm_get_diagnostics(self._h, mass, ctypes.byref(ke), ctypes.byref(hmin))
+        _check(rc, "mlswlbm_get_diagnostics")
+        return np.array(mass[:]), ke.value, hmin.value
+
+    def status(self):
+        return lib().mlswlbm_status(self._h)
+
+    def set_stream(self, stream):
+        _check(lib().mlswlbm_set_stream(self._h, _stream_ptr(stream)), "mlswlbm_set_stream")
+
+    def launch_count(self):
+        return int(lib().mlswlbm_launch_count(self._h))
+
+
+def _checked_out(out, size):
+    if not (isinstance(out, np.ndarray) and out.dtype == np.float32
+            and out.flags["C_CONTIGUOUS"] and out.size == size):
+        raise ValueError("output must be a contiguous float32 array of %d elements" % size)
+    return out
+
+
+def mlswlbm_create(p, h_init, stream=None):
+    return Solver(p, h_init, stream)
+
+
+def mlswlbm_step(s, nsteps=1):
+    s.step(nsteps)
+
+
+def mlswlbm_get_heights(s, out=None):
+    return s.get_heights(out)
+
+
+def mlswlbm_set_heights(s, h):
+    s.set_heights(h)
+
+
+def mlswlbm_get_state(s, out=None):
+    return s.get_state(out)
+
+
+def mlswlbm_set_state(s, f):
+    s.set_state(f)
+
+
+def mlswlbm_save_state(s):
+    return s.save_state()
+
+
+def mlswlbm_load_state(s, H, g):
+    s.load_state(H, g)
+
+
+def mlswlbm_get_diagnostics(s):
+    return s.get_diagnostics()
+
+
+def mlswlbm_status(s):
+    return s.status()
+
+
+def mlswlbm_destroy(s):
+    s.close()
+
+
+def mlswlbm_friction_eval(p, h, Jx, Jy=None, Rx=None, Ry=None, stream=None):
+    """Device tensors [n, ncell]; returns (Rx, Ry)."""
+    import torch
+    s = make_params(p)
+    n = int(p["n"])
+    ncell = h.numel() // n
+    if Rx is None:
+        Rx = torch.empty_like(h)
+    if Jy is not None and Ry is None:
+        Ry = torch.empty_like(h)
+    rc = lib().mlswlbm_friction_eval(
+        ctypes.byref(s), ncell, _dev_ptr(h, n * ncell), _dev_ptr(Jx, n * ncell),
+        _dev_ptr(Jy, n * ncell) if Jy is not None else None, _dev_ptr(Rx, n * ncell),
+        _dev_ptr(Ry, n * ncell) if Ry is not None else None,
+        _stream_ptr(stream if stream is not None else torch.cuda.current_stream()))
+    _check(rc, "mlswlbm_friction_eval")
+    return Rx, Ry

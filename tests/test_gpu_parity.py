@@ -1,0 +1,243 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (FP32 device arithmetic vs FP64 oracle, unit round-off
+u = 2^-24 ~ 6e-8):
+  * heights after many steps: max |h_gpu - h_ref| / max |h_ref| <= 1e-5, the
+    target the solver is specified to;
+  * one step from a given state: every population within 4e-6 * max h. A
+    population is formed from O(50) FP32 operations on O(h) quantities,
+    each contributing at most u * h, and the pressure forces are O(1e-2 h);
+  * friction of independent cells: 1e-4 of the largest |R| of the cell, the
+    FP32 elimination error bound cond(L) * u with cond(L) <= ~1e3 for the
+    thicknesses drawn here;
+  * invariants that the kernels keep exactly (flat film, translation,
+    checkpoint) are compared bit for bit.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from paper_2409_16659_gb300 import mlswlbm as B
+
+pytestmark = pytest.mark.gpu
+
+
+def _f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def _run_both(p, h0, steps):
+    h0 = _f32(h0)
+    with B.Solver(p, h0) as s:
+        s.step(steps)
+        hg = s.get_heights().astype(np.float64)
+    f = oracle.run(p, oracle.init(p, h0.ravel()), steps)
+    return hg, oracle.heights(p, f)
+
+
+def _relmax(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+def test_film2_d1q3_512_cells_1000_steps():
+    p = workloads.film2_d1q3_params(512)
+    hg, hr = _run_both(p, workloads.film2_d1q3_heights(512), 1000)
+    assert _relmax(hg, hr) <= 1e-5
+
+
+def test_film3_d2q9_ragged_1000_steps():
+    # 72 x 40 cells: 3 x 3 tiles of 32 x 16, ragged in both directions
+    p = workloads.film3_d2q9_params(72, 40)
+    hg, hr = _run_both(p, workloads.film3_d2q9_heights(72, 40), 1000)
+    assert _relmax(hg, hr) <= 1e-5
+
+
+# -- the seeded cases (also checked on the CPU for create-time stability) ----
+ONE_STEP = [(n, lat, tau) for n in (1, 2, 3, 4, 5)
+            for lat, tau in ((2, 1.0), (2, 0.8), (1, 1.0), (1, 1.4))]
+MULTISTEP = [2, 4, 5]
+EDGE = [(2, 1, 1), (2, 2, 3), (2, 1, 7), (2, 5, 1), (2, 33, 17),
+        (1, 1, 1), (1, 2, 1), (1, 3, 1), (1, 129, 1)]
+
+
+def one_step_case(n, lat, tau):
+    nx, ny = (37, 21) if lat == 2 else (301, 1)
+    p = workloads.random_params(40 + n, n, lat, nx, ny, tau=tau)
+    return p, _f32(workloads.random_populations(50 + n, p, 0.5, 1.0, 2e-3))
+
+
+def multistep_case(n):
+    p = workloads.random_params(70 + n, n, 2, 45, 33)
+    return p, workloads.random_heights(80 + n, p, 0.5, 1.1, 2e-3)
+
+
+def edge_case(lat, nx, ny):
+    p = workloads.random_params(90 + nx + ny, 3, lat, nx, ny)
+    return p, workloads.random_heights(91 + nx, p, 0.6, 1.0, 5e-3)
+
+
+@pytest.mark.parametrize("n,lat,tau", ONE_STEP)
+def test_one_step_from_random_state(n, lat, tau):
+    p, f = one_step_case(n, lat, tau)
+    hmax = oracle.heights(p, f).max()
+    with B.Solver(p, oracle.heights(p, f)) as s:
+        s.set_state(f)
+        s.step(1)
+        fg = s.get_state().astype(np.float64)
+        assert s.status() == B.MLSW_OK
+    fr = oracle.step(p, f)
+    assert np.abs(fg - fr).max() <= 4e-6 * hmax
+
+
+@pytest.mark.parametrize("n", MULTISTEP)
+def test_random_params_multistep(n):
+    p, h0 = multistep_case(n)
+    hg, hr = _run_both(p, h0, 300)
+    assert _relmax(hg, hr) <= 1e-5
+
+
+@pytest.mark.parametrize("lat,nx,ny", EDGE)
+def test_degenerate_and_edge_sizes(lat, nx, ny):
+    p, h0 = edge_case(lat, nx, ny)
+    hg, hr = _run_both(p, h0, 25)
+    assert _relmax(hg, hr) <= 1e-5
+
+
+def test_flat_film_stays_bit_exact():
+    p = workloads.film3_d2q9_params(50, 30)
+    h0 = np.broadcast_to(np.array([1.0, 0.8, 0.6])[:, None, None], (3, 30, 50)).copy()
+    with B.Solver(p, h0) as s:
+        f0 = s.get_state()
+        s.step(200)
+        assert np.array_equal(s.get_state(), f0)
+
+
+def test_mass_conserved_to_fp32_roundoff():
+    p = workloads.film3_d2q9_params(128, 96)
+    h0 = _f32(workloads.film3_d2q9_heights(128, 96))
+    with B.Solver(p, h0) as s:
+        m0, _, _ = s.get_diagnostics()
+        s.step(2000)
+        m1, ke, hmin = s.get_diagnostics()
+    np.testing.assert_allclose(m0, h0.sum(axis=(1, 2)), rtol=1e-12)
+    assert np.abs(m1 - m0).max() / m0.max() <= 1e-6
+    assert hmin > 0.5 and np.isfinite(ke)
+
+
+def test_translation_equivariance_bit_exact():
+    p = workloads.film3_d2q9_params(70, 36)
+    h0 = workloads.film3_d2q9_heights(70, 36)
+    hs = np.roll(h0, (5, -11), axis=(1, 2))
+    with B.Solver(p, h0) as a, B.Solver(p, hs) as b:
+        a.step(20)
+        b.step(20)
+        assert np.array_equal(np.roll(a.get_heights(), (5, -11), axis=(1, 2)), b.get_heights())
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5])
+def test_friction_eval_matches_oracle(n):
+    import torch
+    rng = np.random.default_rng(200 + n)
+    ncell = 257
+    p = workloads.random_params(300 + n, n, 2, 1, 1)
+    p["beta"] = list(rng.uniform(0.0, 1.5, n))
+    p["beta"][0] = 0.0 if n % 2 else p["beta"][0]
+    h = rng.uniform(0.06, 1.5, (n, ncell)).astype(np.float32)
+    Jx = rng.normal(0, 1e-3, (n, ncell)).astype(np.float32)
+    Jy = rng.normal(0, 1e-3, (n, ncell)).astype(np.float32)
+    dev = lambda a: torch.from_numpy(a).cuda().contiguous()
+    Rx, Ry = B.mlswlbm_friction_eval(p, dev(h), dev(Jx), dev(Jy))
+    torch.cuda.synchronize()
+    Rx, Ry = Rx.cpu().numpy().astype(np.float64), Ry.cpu().numpy().astype(np.float64)
+    for c in range(ncell):
+        rx, ry = oracle.friction(p, h[:, c].astype(np.float64), Jx[:, c].astype(np.float64),
+                                 Jy[:, c].astype(np.float64))
+        scale = max(np.abs(rx).max(), np.abs(ry).max())
+        assert np.abs(Rx[:, c] - rx).max() <= 1e-4 * scale + 1e-12
+        assert np.abs(Ry[:, c] - ry).max() <= 1e-4 * scale + 1e-12
+
+
+def test_full_size_film3_1024_in_bench_configuration():
+    """The 1024 x 1024 three-layer workload in the launch configuration the
+    benchmark times: three steps from a seeded non-equilibrium state, every
+    population compared with the oracle."""
+    p = workloads.film3_d2q9_params(1024, 1024)
+    f = _f32(workloads.random_populations(7, p, 0.55, 1.05, 1e-3))
+    hmax = oracle.heights(p, f).max()
+    with B.Solver(p, oracle.heights(p, f)) as s:
+        s.set_state(f)
+        s.step(3)
+        fg = s.get_state().astype(np.float64)
+    fr = f
+    for _ in range(3):
+        fr = oracle.step(p, fr)
+    assert np.abs(fg - fr).max() <= 3 * 4e-6 * hmax
+
+
+def test_nonfinite_state_is_reported():
+    p = workloads.film3_d2q9_params(40, 20)
+    h0 = workloads.film3_d2q9_heights(40, 20)
+    with B.Solver(p, h0) as s:
+        f = s.get_state()
+        f[1, 0, 7, 9] = np.nan
+        s.set_state(f)
+        s.step(1)
+        assert s.status() == B.MLSW_ERR_NONFINITE
+        assert s.status() == B.MLSW_OK  # cleared by the query
+        h = np.array(h0, dtype=np.float32)
+        h[2, 3, 3] = -0.5
+        s.set_heights(h)
+        with pytest.raises(B.MlswError) as e:
+            s.get_heights()
+        assert e.value.code == B.MLSW_ERR_NONFINITE
+
+
+def test_checkpoint_resume_bit_exact():
+    p = workloads.film3_d2q9_params(64, 48)
+    h0 = workloads.film3_d2q9_heights(64, 48)
+    with B.Solver(p, h0) as s, B.Solver(p, np.ones_like(h0)) as t:
+        s.step(10)
+        H, g = s.save_state()
+        s.step(15)
+        a = s.save_state()[1]
+        t.load_state(H, g)  # a second handle resumes from the checkpoint
+        t.step(15)
+        assert np.array_equal(t.save_state()[1], a)
+        assert np.array_equal(t.get_heights(), s.get_heights())
+
+
+def test_state_get_set_roundtrip_is_exact_in_true_populations():
+    p = workloads.film3_d2q9_params(40, 20)
+    f = _f32(workloads.random_populations(23, p, 0.5, 1.0, 2e-3))
+    with B.Solver(p, oracle.heights(p, f)) as s:
+        s.set_state(f)
+        # f_0 and H_i lie within a factor two of each other, so f_0 - H_i and
+        # H_i + (f_0 - H_i) are exact in FP32
+        assert np.array_equal(s.get_state().astype(np.float64), f)
+
+
+def test_heights_roundtrip_and_diagnostics():
+    p = workloads.film3_d2q9_params(48, 40)
+    f = _f32(workloads.random_populations(17, p, 0.5, 1.0, 2e-3))
+    h, Jx, Jy = oracle.moments(p, f)
+    with B.Solver(p, h) as s:
+        h32 = np.asarray(h, dtype=np.float32)
+        assert np.array_equal(s.get_heights(), h32)
+        s.set_state(f)
+        mass, ke, hmin = s.get_diagnostics()
+    np.testing.assert_allclose(mass, h.sum(axis=(1, 2)), rtol=1e-6)
+    assert ke == pytest.approx(((Jx ** 2 + Jy ** 2) / (2 * h)).sum(), rel=1e-4)
+    assert hmin == pytest.approx(h.min(), rel=1e-6)
+
+
+def test_torch_stream_binding_and_launch_count():
+    import torch
+    p = workloads.film2_d1q3_params(512)
+    h0 = workloads.film2_d1q3_heights(512)
+    st = torch.cuda.Stream()
+    with B.Solver(p, h0, stream=st) as a, B.Solver(p, h0) as b:
+        a.step(40)
+        b.step(40)
+        assert np.array_equal(a.get_heights(), b.get_heights())
+        assert a.launch_count() == 1 + 40 + 1  # init, steps, height read-out
