@@ -199,6 +199,37 @@ int mlswlbm_friction_eval(const mlsw_params* p, long ncell, const float* h,
                           const float* Jx, const float* Jy, float* Rx,
                           float* Ry, void* stream);
 
+/*
+ * Diagnostics without any allocation. The paper has no counterpart; this
+ * entry point serves callers that cannot call cudaMalloc: applications
+ * whose device memory is already reserved by a pool allocator (a plain
+ * cudaMalloc there fails or fragments the pool) and latency-critical loops
+ * in which cudaMalloc / cudaFree would synchronise the whole device.
+ *
+ * Computes what mlswlbm_get_diagnostics computes -- out[i] = mass of layer
+ * i (i < n), out[n] = kinetic energy sum |J|^2 / (2h), out[n+1] = min h --
+ * for a population array that the caller owns, without a handle.
+ *   p       problem statement; n_layers, lattice, nx, ny are used.
+ *   f       device, n*Q*nx*ny floats in the population layout above.
+ *   H       host, n floats: the rest planes of f hold f_0 - H_i (as written
+ *           by mlswlbm_save_state); NULL when f holds the true populations.
+ *   out     device, n + 2 doubles, caller-owned; written asynchronously.
+ *   stream  cudaStream_t or NULL.
+ * Scratch: a static device array of 224 KiB (4096 blocks x 7 doubles) in
+ * the library, held by every GPU that loads the library until exit. One
+ * block is used per 16384 cells, so lattices above 4096 * 16384 cells
+ * (67,108,864) return MLSW_ERR_UNSUPPORTED. The first call on a device looks
+ * up the array's device address (with that device current) and should come
+ * before any stream capture. Every call shares the array and overwrites
+ * the partials it uses; calls that overlap on the GPU race on it. Calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ * Errors: MLSW_ERR_ARG (NULL pointer, invalid p, non-finite H),
+ * MLSW_ERR_UNSUPPORTED (lattice beyond the scratch, device ordinal >= 64),
+ * MLSW_ERR_CUDA (symbol look-up or launch failed).
+ */
+int mlswlbm_diagnostics_noalloc(const mlsw_params* p, const float* f, const float* H,
+                                double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,67 @@
+// noalloc.cu -- mlswlbm_diagnostics_noalloc: the diagnostics reduction with
+// its scratch in a static device array, for callers that cannot allocate.
+//
+// Some callers cannot call cudaMalloc: applications whose device memory is
+// already reserved by a pool allocator (a plain cudaMalloc then fails or
+// fragments the pool), and latency-critical loops in which cudaMalloc /
+// cudaFree would synchronise the whole device. This entry point needs no
+// handle and allocates nothing: the per-block partial sums live in
+// g_diag_scratch below, which every GPU that loads the library holds until
+// the process exits.
+#include <cmath>
+#include <mutex>
+
+#include "../../include/mlswlbm.h"
+#include "kernels.h"
+#include "physics.cuh"
+
+namespace {
+
+// Each reduction block sums a fixed run of cells, so the partials needed
+// grow with the lattice; the array holds kNoallocBlocks blocks of
+// (MLSW_MAX_LAYERS + 2) doubles = 224 KiB.
+constexpr long kNoallocCellsPerBlock = 16384;
+constexpr int kNoallocBlocks = 4096;
+constexpr int kNoallocMaxDevices = 64;
+
+static __device__ __align__(256) double g_diag_scratch[kNoallocBlocks * (MLSW_MAX_LAYERS + 2)];
+
+std::once_flag g_once[kNoallocMaxDevices];
+cudaError_t g_setup_err[kNoallocMaxDevices];
+double* g_scratch_ptr[kNoallocMaxDevices];
+
+// The host-side name g_diag_scratch is only a stand-in for the device
+// array; its device address is looked up once per device, with that device
+// current, and passed to the kernels.
+void setup_device(int dev) {
+  void* ptr = nullptr;
+  g_setup_err[dev] = cudaGetSymbolAddress(&ptr, g_diag_scratch);
+  g_scratch_ptr[dev] = (g_setup_err[dev] == cudaSuccess) ? static_cast<double*>(ptr) : nullptr;
+}
+
+}  // namespace
+
+extern "C" int mlswlbm_diagnostics_noalloc(const mlsw_params* p, const float* f,
+                                           const float* H, double* out, void* stream) {
+  if (!p || !f || !out) return MLSW_ERR_ARG;
+  if (mlswlbm_check_params(p) != MLSW_OK) return MLSW_ERR_ARG;
+  const int n = p->n_layers;
+  const long ncell = (long)p->nx * p->ny;
+  const long nblk = (ncell + kNoallocCellsPerBlock - 1) / kNoallocCellsPerBlock;
+  if (nblk > kNoallocBlocks) return MLSW_ERR_UNSUPPORTED;  // beyond the static scratch
+  mlsw::KShift sh;
+  for (int i = 0; i < mlsw::kMaxLayers; ++i) {
+    sh.H[i] = (H && i < n) ? H[i] : 0.f;
+    if (!std::isfinite(sh.H[i])) return MLSW_ERR_ARG;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MLSW_ERR_CUDA;
+  if (dev < 0 || dev >= kNoallocMaxDevices) return MLSW_ERR_UNSUPPORTED;
+  std::call_once(g_once[dev], setup_device, dev);
+  if (g_setup_err[dev] != cudaSuccess || !g_scratch_ptr[dev]) return MLSW_ERR_CUDA;
+  // every block writes its own partials, so nothing needs clearing first
+  const cudaError_t e =
+      mlsw::launch_diagnostics(p->lattice, n, ncell, f, sh, g_scratch_ptr[dev], (int)nblk, out,
+                               (cudaStream_t)stream);
+  return e == cudaSuccess ? MLSW_OK : MLSW_ERR_CUDA;
+}

@@ -82,6 +82,8 @@ EXPORTS = {
     "mlswlbm_launch_count": (ctypes.c_long, [_H]),
     "mlswlbm_destroy": (None, [_H]),
     "mlswlbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "mlswlbm_diagnostics_noalloc": (ctypes.c_int, [_P, ctypes.c_void_p, _F,
+                                                   ctypes.c_void_p, ctypes.c_void_p]),
     "mlswlbm_friction_eval": (ctypes.c_int, [_P, ctypes.c_long, ctypes.c_void_p,
                                              ctypes.c_void_p, ctypes.c_void_p,
                                              ctypes.c_void_p, ctypes.c_void_p,
@@ -354,3 +356,25 @@ def mlswlbm_friction_eval(p, h, Jx, Jy=None, Rx=None, Ry=None, stream=None):
         _stream_ptr(stream if stream is not None else torch.cuda.current_stream()))
     _check(rc, "mlswlbm_friction_eval")
     return Rx, Ry
+
+
+def mlswlbm_diagnostics_noalloc(p, f, out, H=None, stream=None):
+    """Diagnostics of a caller-owned device population array, allocating
+    nothing: f is a float32 CUDA tensor of n*Q*nx*ny elements, out a float64
+    CUDA tensor of n + 2 elements (mass per layer, kinetic energy, min h);
+    H (n floats) when f holds the shifted rest planes of save_state."""
+    import torch
+    s = make_params(p)
+    n = int(p["n"])
+    q = 3 if int(p.get("lattice", 2)) == MLSW_D1Q3 else 9
+    numel = n * q * int(p.get("nx", 1)) * int(p.get("ny", 1))
+    if not (isinstance(out, torch.Tensor) and out.is_cuda and out.dtype == torch.float64
+            and out.is_contiguous() and out.numel() == n + 2):
+        raise ValueError("out must be a contiguous float64 CUDA tensor of n + 2 elements")
+    Ha = None if H is None else _host_f32(H, n)
+    rc = lib().mlswlbm_diagnostics_noalloc(
+        ctypes.byref(s), _dev_ptr(f, numel), None if Ha is None else _fptr(Ha),
+        ctypes.c_void_p(out.data_ptr()),
+        _stream_ptr(stream if stream is not None else torch.cuda.current_stream()))
+    _check(rc, "mlswlbm_diagnostics_noalloc")
+    return out
