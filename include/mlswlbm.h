@@ -117,7 +117,9 @@ int mlswlbm_check_params(const mlsw_params* p);
  * a uniform flux, J <- (1 + K) J with the friction matrix K of
  * Eq. (friction_force), must be contractive at the per-layer minimum, mean
  * and maximum of h_init and with every layer at h*; otherwise
- * MLSW_ERR_UNSTABLE. stream: cudaStream_t or NULL.
+ * MLSW_ERR_UNSTABLE. MLSW_ERR_UNSUPPORTED when one layer's padded planes
+ * exceed 2^31 - 1 floats (about 15000 x 15000 cells for D2Q9).
+ * stream: cudaStream_t or NULL.
  * On failure *out is set to NULL and nothing is leaked.
  */
 int mlswlbm_create(const mlsw_params* p, const float* h_init, void* stream,

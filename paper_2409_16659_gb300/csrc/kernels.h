@@ -1,48 +1,87 @@
 // kernels.h -- internal launch interface between the host library
-// (mlswlbm.cu) and the kernel translation units. Not part of the C ABI.
+// (mlswlbm.cu, noalloc.cu) and the kernel translation units. Not part of
+// the C ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "physics.cuh"
 
 namespace mlsw {
 
+// status word bits (device int OR-ed by the kernels)
+constexpr int kStatusNonfinite = 1;  // h <= 0 or a non-finite value
+constexpr int kStatusTimeout = 2;    // a bounded mbarrier wait ran out
+
 // Per-layer rest-population shift (see KParams).
 struct KShift {
   float H[kMaxLayers];
 };
 
-// One fused time step fin -> fout (distinct buffers) for lattice 1 (D1Q3)
-// or 2 (D2Q9). status: device int, OR-ed with 1 on h <= 0 / non-finite.
-cudaError_t launch_step(int lattice, const float* fin, float* fout, const KParams& P, int* status,
-                        cudaStream_t st);
+// One fused time step fin -> fout (distinct buffers, layout P.L).
+struct StepLaunch {
+  int lattice;                  // 1 = D1Q3, 2 = D2Q9
+  const float* fin;
+  float* fout;
+  const CUtensorMap* fin_map;   // D2Q9: 3-D tensor map of fin (box of one tile)
+  KParams P;
+  int* status;
+  int* sched;                   // D2Q9: two zero-initialised tile-scheduler counters
+  int num_sms;
+};
+cudaError_t launch_step(const StepLaunch& a, cudaStream_t st);
 
-// f = f_eq(h, U = 0): rest population = h (stored as h - H_i), moving
-// populations = 0. status is OR-ed with 1 where h <= 0 or h is not finite.
-cudaError_t launch_init(int Q, int n, long ncell, const float* h, float* f, const KShift& sh,
+// Tile shape of the step kernels (the padded layout covers whole tiles).
+int step_tile_cols(int lattice);
+int step_tile_rows(int n, int lattice);
+
+// f = f_eq(h, U = 0) on the real cells: rest population h - H_i, moving
+// populations 0; h dense [n][ny][nx]. status |= kStatusNonfinite where
+// h <= 0 or h is not finite. Ghost cells are left to launch_fill_ghosts.
+cudaError_t launch_init(int Q, int n, const Layout& L, const float* h, float* f, const KShift& sh,
                         int* status, cudaStream_t st);
 
-// h[i][cell] = H_i + sum_k g[i][k][cell]
-cudaError_t launch_heights(int Q, int n, long ncell, const float* f, const KShift& sh, float* h,
-                           cudaStream_t st);
+// Periodic images: every ghost cell within two cells of the real domain
+// (x only when ghosts_y is false) copies its real cell, for all nplanes
+// planes.
+cudaError_t launch_fill_ghosts(int nplanes, const Layout& L, bool ghosts_y, float* f,
+                               cudaStream_t st);
 
-// rest-population planes: f[i][0] += sign * H_i (sign = +1 or -1)
-cudaError_t launch_shift(int Q, int n, long ncell, float* f, const KShift& sh, float sign,
+// h dense [n][ny][nx] = H_i + sum_k g[i][k]
+cudaError_t launch_heights(int Q, int n, const Layout& L, const float* f, const KShift& sh,
+                           float* h, cudaStream_t st);
+
+// real cells of the rest planes: f[i][0] += sign * H_i
+cudaError_t launch_shift(int Q, int n, const Layout& L, float* f, const KShift& sh, float sign,
                          cudaStream_t st);
 
-// out[i][cell] = H_i + g[i][0][cell], the true rest population
-cudaError_t launch_rest_planes(int Q, int n, long ncell, const float* f, const KShift& sh,
+// out dense [n][ny][nx] = H_i + g[i][0], the true rest population
+cudaError_t launch_rest_planes(int Q, int n, const Layout& L, const float* f, const KShift& sh,
                                float* out, cudaStream_t st);
 
 // Two-pass deterministic reduction of per-layer mass, kinetic energy and
-// min h. partials: nblk * (n + 2) doubles; out: n + 2 doubles
-// (mass[0..n-1], kinetic, hmin).
-cudaError_t launch_diagnostics(int lattice, int n, long ncell, const float* f, const KShift& sh,
-                               double* partials, int nblk, double* out, cudaStream_t st);
+// min h over the real cells. partials: nblk * (n + 2) doubles; out: n + 2
+// doubles (mass[0..n-1], kinetic, hmin).
+cudaError_t launch_diagnostics(int lattice, int n, const Layout& L, const float* f,
+                               const KShift& sh, double* partials, int nblk, double* out,
+                               cudaStream_t st);
 
 // Friction of independent cells (layout [i][cell]); Jy / Ry may be null.
 cudaError_t launch_friction_eval(const KParams& P, long ncell, const float* h, const float* Jx,
                                  const float* Jy, float* Rx, float* Ry, cudaStream_t st);
+
+// Dense layout of a caller-owned population array (no ghosts).
+inline Layout dense_layout(int nx, int ny) {
+  Layout L;
+  L.nx = nx;
+  L.ny = ny;
+  L.gx = 0;
+  L.gy = 0;
+  L.pitch = nx;
+  L.rows = ny;
+  L.plane = (long)nx * ny;
+  return L;
+}
 
 }  // namespace mlsw

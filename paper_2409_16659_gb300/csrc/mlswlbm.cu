@@ -14,20 +14,22 @@ using mlsw::KParams;
 
 struct mlsw_handle {
   mlsw_params p;
-  KParams kp;
+  KParams kp;         // includes the padded layout kp.L
   int Q;
   long ncell;
-  size_t flen;        // floats per population buffer
+  size_t flen;        // floats per (padded) population buffer
   float* f[2];
   int cur;            // index of the buffer holding the current state
   float* hbuf;        // n * ncell heights (upload / read-out)
-  int* status;        // device flag, OR of kernel error bits
+  int* status;        // [0] OR of kernel error bits; [1], [2] tile scheduler
   double* partials;   // diagnostics partials
   double* dout;       // diagnostics result, n + 2 doubles
   int nblk_diag;
   cudaStream_t stream;
   long launches;
   mlsw::KShift sh;    // rest-population shift H_i (also in kp.H)
+  int num_sms;
+  CUtensorMap map[2]; // D2Q9: tensor map of each buffer, box = one tile + halo
 };
 
 namespace {
@@ -143,6 +145,94 @@ int check_heights(const mlsw_params& p, const float* h) {
   do {                                               \
     if ((call) != cudaSuccess) return MLSW_ERR_CUDA; \
   } while (0)
+
+// ---------------------------------------------------------------------------
+// padded layout and tensor maps
+// ---------------------------------------------------------------------------
+int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+mlsw::Layout make_layout(const mlsw_params& p) {
+  mlsw::Layout L;
+  const int tx = mlsw::step_tile_cols(p.lattice);
+  const int ty = mlsw::step_tile_rows(p.n_layers, p.lattice);
+  L.nx = p.nx;
+  L.ny = p.ny;
+  L.gx = 4;  // two ghost columns plus two for 16-byte alignment of tile boxes
+  L.gy = (p.lattice == MLSW_D2Q9) ? 2 : 0;
+  L.pitch = round_up(p.nx, tx) + 8;
+  L.rows = (p.lattice == MLSW_D2Q9) ? round_up(p.ny, ty) + 4 : 1;
+  L.plane = (long)L.pitch * L.rows;
+  return L;
+}
+
+int wrap_host(int v, int n) {
+  v %= n;
+  return v < 0 ? v + n : v;
+}
+
+void set_ghost_tables(KParams& k, const mlsw_params& p) {
+  const int gx[4] = {-2, -1, p.nx, p.nx + 1};
+  const int gy[4] = {-2, -1, p.ny, p.ny + 1};
+  for (int g = 0; g < 4; ++g) {
+    k.gsrcx[g] = wrap_host(gx[g], p.nx);
+    k.gsrcy[g] = (p.lattice == MLSW_D2Q9) ? wrap_host(gy[g], p.ny) : -1000;
+  }
+  k.tiny = (p.nx < 4 || (p.lattice == MLSW_D2Q9 && p.ny < 4)) ? 1 : 0;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(ptr);
+  }
+  return fn;
+}
+
+// 3-D map (x: pitch, y: rows, z: planes) whose box is one D2Q9 tile with
+// its halo: 40 x (TY + 4) x all planes.
+bool make_tile_map(CUtensorMap* m, float* base, const mlsw::Layout& L, int nplanes, int ty) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)L.pitch, (cuuint64_t)L.rows, (cuuint64_t)nplanes};
+  cuuint64_t strides[2] = {(cuuint64_t)L.pitch * 4, (cuuint64_t)L.plane * 4};
+  cuuint32_t box[3] = {(cuuint32_t)(mlsw::step_tile_cols(MLSW_D2Q9) + 8), (cuuint32_t)(ty + 4),
+                       (cuuint32_t)nplanes};
+  cuuint32_t es[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
+// host <-> device copies of the real cells of every plane
+cudaError_t copy_planes(mlsw_handle* h, float* host, const float* dev, bool to_host) {
+  const mlsw::Layout& L = h->kp.L;
+  const int nplanes = h->p.n_layers * h->Q;
+  const size_t row = (size_t)L.nx * sizeof(float);
+  for (int pl = 0; pl < nplanes; ++pl) {
+    float* hp = host + (size_t)pl * h->ncell;
+    const float* dp = dev + L.at(pl, 0, 0);
+    cudaError_t e =
+        to_host ? cudaMemcpy2DAsync(hp, row, dp, (size_t)L.pitch * sizeof(float), row, L.ny,
+                                    cudaMemcpyDeviceToHost, h->stream)
+                : cudaMemcpy2DAsync(const_cast<float*>(dp), (size_t)L.pitch * sizeof(float), hp,
+                                    row, row, L.ny, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
 
 void set_shift(mlsw_handle* h, const float* H) {
   for (int i = 0; i < mlsw::kMaxLayers; ++i) {
@@ -268,7 +358,14 @@ int mlswlbm_create(const mlsw_params* p, const float* h_init, void* stream, mlsw
   h->kp = make_kparams(*p);
   h->Q = Qof(p->lattice);
   h->ncell = ncell;
-  h->flen = (size_t)n * h->Q * ncell;
+  h->kp.L = make_layout(*p);
+  // the step kernels address a layer's planes with 32-bit offsets
+  if ((double)h->kp.L.plane * h->Q >= 2147483647.0) {
+    delete h;
+    return MLSW_ERR_UNSUPPORTED;
+  }
+  set_ghost_tables(h->kp, *p);
+  h->flen = (size_t)n * h->Q * h->kp.L.plane;
   h->stream = (cudaStream_t)stream;
   set_shift(h, shift);
   int dev = 0, sms = 0;
@@ -277,11 +374,12 @@ int mlswlbm_create(const mlsw_params* p, const float* h_init, void* stream, mlsw
     delete h;
     return MLSW_ERR_CUDA;
   }
-  h->nblk_diag = 2 * (sms > 0 ? sms : 1);
+  h->num_sms = sms > 0 ? sms : 1;
+  h->nblk_diag = 2 * h->num_sms;
   bool ok = cudaMalloc(&h->f[0], h->flen * sizeof(float)) == cudaSuccess &&
             cudaMalloc(&h->f[1], h->flen * sizeof(float)) == cudaSuccess &&
             cudaMalloc(&h->hbuf, (size_t)n * ncell * sizeof(float)) == cudaSuccess &&
-            cudaMalloc(&h->status, sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&h->status, 4 * sizeof(int)) == cudaSuccess &&
             cudaMalloc(&h->partials, (size_t)h->nblk_diag * (n + 2) * sizeof(double)) ==
                 cudaSuccess &&
             cudaMalloc(&h->dout, (size_t)(n + 2) * sizeof(double)) == cudaSuccess;
@@ -290,9 +388,21 @@ int mlswlbm_create(const mlsw_params* p, const float* h_init, void* stream, mlsw
     mlswlbm_destroy(h);
     return MLSW_ERR_NOMEM;
   }
-  if (cudaMemsetAsync(h->status, 0, sizeof(int), h->stream) != cudaSuccess) {
+  // zero padding: cells outside the real domain and its ghost ring are read
+  // by edge tiles but never feed a real cell
+  if (cudaMemsetAsync(h->status, 0, 4 * sizeof(int), h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->f[0], 0, h->flen * sizeof(float), h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->f[1], 0, h->flen * sizeof(float), h->stream) != cudaSuccess) {
     mlswlbm_destroy(h);
     return MLSW_ERR_CUDA;
+  }
+  if (p->lattice == MLSW_D2Q9) {
+    const int ty = mlsw::step_tile_rows(n, p->lattice);
+    if (!make_tile_map(&h->map[0], h->f[0], h->kp.L, n * h->Q, ty) ||
+        !make_tile_map(&h->map[1], h->f[1], h->kp.L, n * h->Q, ty)) {
+      mlswlbm_destroy(h);
+      return MLSW_ERR_CUDA;
+    }
   }
   rc = mlswlbm_set_heights(h, h_init);
   if (rc == MLSW_OK && cudaStreamSynchronize(h->stream) != cudaSuccess) rc = MLSW_ERR_CUDA;
@@ -308,18 +418,27 @@ int mlswlbm_set_heights(mlsw_handle* h, const float* h_in) {
   if (!h || !h_in) return MLSW_ERR_ARG;
   const size_t bytes = (size_t)h->p.n_layers * h->ncell * sizeof(float);
   CU(cudaMemcpyAsync(h->hbuf, h_in, bytes, cudaMemcpyHostToDevice, h->stream));
-  CU(mlsw::launch_init(h->Q, h->p.n_layers, h->ncell, h->hbuf, h->f[h->cur], h->sh,
-                       h->status, h->stream));
-  h->launches += 1;
+  CU(mlsw::launch_init(h->Q, h->p.n_layers, h->kp.L, h->hbuf, h->f[h->cur], h->sh, h->status,
+                       h->stream));
+  CU(mlsw::launch_fill_ghosts(h->p.n_layers * h->Q, h->kp.L, h->p.lattice == MLSW_D2Q9,
+                              h->f[h->cur], h->stream));
+  h->launches += 2;
   return MLSW_OK;
 }
 
 int mlswlbm_step(mlsw_handle* h, long nsteps) {
   if (!h || nsteps < 0) return MLSW_ERR_ARG;
+  mlsw::StepLaunch a;
+  a.lattice = h->p.lattice;
+  a.P = h->kp;
+  a.status = h->status;
+  a.sched = h->status + 1;
+  a.num_sms = h->num_sms;
   for (long s = 0; s < nsteps; ++s) {
-    const float* fin = h->f[h->cur];
-    float* fout = h->f[h->cur ^ 1];
-    CU(mlsw::launch_step(h->p.lattice, fin, fout, h->kp, h->status, h->stream));
+    a.fin = h->f[h->cur];
+    a.fout = h->f[h->cur ^ 1];
+    a.fin_map = &h->map[h->cur];
+    CU(mlsw::launch_step(a, h->stream));
     h->cur ^= 1;
     h->launches += 1;
   }
@@ -333,14 +452,14 @@ int mlswlbm_status(mlsw_handle* h) {
   CU(cudaStreamSynchronize(h->stream));
   if (flag) {
     CU(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
-    return MLSW_ERR_NONFINITE;
+    return (flag & mlsw::kStatusTimeout) ? MLSW_ERR_TIMEOUT : MLSW_ERR_NONFINITE;
   }
   return MLSW_OK;
 }
 
 int mlswlbm_get_heights_device(mlsw_handle* h, float* dev_out) {
   if (!h || !dev_out) return MLSW_ERR_ARG;
-  CU(mlsw::launch_heights(h->Q, h->p.n_layers, h->ncell, h->f[h->cur], h->sh, dev_out,
+  CU(mlsw::launch_heights(h->Q, h->p.n_layers, h->kp.L, h->f[h->cur], h->sh, dev_out,
                           h->stream));
   h->launches += 1;
   return MLSW_OK;
@@ -361,10 +480,9 @@ int mlswlbm_get_state(mlsw_handle* h, float* f_out) {
   const size_t plane = (size_t)h->ncell;
   // rest planes H_i + g_0 into the height buffer, all planes raw to the host,
   // then the rest planes over their raw copies
-  CU(mlsw::launch_rest_planes(h->Q, n, h->ncell, h->f[h->cur], h->sh, h->hbuf, h->stream));
+  CU(mlsw::launch_rest_planes(h->Q, n, h->kp.L, h->f[h->cur], h->sh, h->hbuf, h->stream));
   h->launches += 1;
-  CU(cudaMemcpyAsync(f_out, h->f[h->cur], h->flen * sizeof(float), cudaMemcpyDeviceToHost,
-                     h->stream));
+  CU(copy_planes(h, f_out, h->f[h->cur], true));
   for (int i = 0; i < n; ++i)
     CU(cudaMemcpyAsync(f_out + (size_t)i * h->Q * plane, h->hbuf + (size_t)i * plane,
                        plane * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
@@ -374,10 +492,11 @@ int mlswlbm_get_state(mlsw_handle* h, float* f_out) {
 
 int mlswlbm_set_state(mlsw_handle* h, const float* f_in) {
   if (!h || !f_in) return MLSW_ERR_ARG;
-  CU(cudaMemcpyAsync(h->f[h->cur], f_in, h->flen * sizeof(float), cudaMemcpyHostToDevice,
-                     h->stream));
-  CU(mlsw::launch_shift(h->Q, h->p.n_layers, h->ncell, h->f[h->cur], h->sh, -1.f, h->stream));
-  h->launches += 1;
+  CU(copy_planes(h, const_cast<float*>(f_in), h->f[h->cur], false));
+  CU(mlsw::launch_shift(h->Q, h->p.n_layers, h->kp.L, h->f[h->cur], h->sh, -1.f, h->stream));
+  CU(mlsw::launch_fill_ghosts(h->p.n_layers * h->Q, h->kp.L, h->p.lattice == MLSW_D2Q9,
+                              h->f[h->cur], h->stream));
+  h->launches += 2;
   CU(cudaStreamSynchronize(h->stream));
   return MLSW_OK;
 }
@@ -385,8 +504,7 @@ int mlswlbm_set_state(mlsw_handle* h, const float* f_in) {
 int mlswlbm_save_state(mlsw_handle* h, float* H_out, float* g_out) {
   if (!h || !H_out || !g_out) return MLSW_ERR_ARG;
   for (int i = 0; i < h->p.n_layers; ++i) H_out[i] = h->sh.H[i];
-  CU(cudaMemcpyAsync(g_out, h->f[h->cur], h->flen * sizeof(float), cudaMemcpyDeviceToHost,
-                     h->stream));
+  CU(copy_planes(h, g_out, h->f[h->cur], true));
   CU(cudaStreamSynchronize(h->stream));
   return MLSW_OK;
 }
@@ -397,8 +515,10 @@ int mlswlbm_load_state(mlsw_handle* h, const float* H_in, const float* g_in) {
     if (!std::isfinite(H_in[i])) return MLSW_ERR_ARG;
   CU(cudaStreamSynchronize(h->stream));
   set_shift(h, H_in);
-  CU(cudaMemcpyAsync(h->f[h->cur], g_in, h->flen * sizeof(float), cudaMemcpyHostToDevice,
-                     h->stream));
+  CU(copy_planes(h, const_cast<float*>(g_in), h->f[h->cur], false));
+  CU(mlsw::launch_fill_ghosts(h->p.n_layers * h->Q, h->kp.L, h->p.lattice == MLSW_D2Q9,
+                              h->f[h->cur], h->stream));
+  h->launches += 1;
   CU(cudaStreamSynchronize(h->stream));
   return MLSW_OK;
 }
@@ -406,7 +526,7 @@ int mlswlbm_load_state(mlsw_handle* h, const float* H_in, const float* g_in) {
 int mlswlbm_get_diagnostics(mlsw_handle* h, double* mass, double* kinetic, double* hmin) {
   if (!h) return MLSW_ERR_ARG;
   const int n = h->p.n_layers;
-  CU(mlsw::launch_diagnostics(h->p.lattice, n, h->ncell, h->f[h->cur], h->sh, h->partials,
+  CU(mlsw::launch_diagnostics(h->p.lattice, n, h->kp.L, h->f[h->cur], h->sh, h->partials,
                               h->nblk_diag, h->dout, h->stream));
   h->launches += 2;
   double res[MLSW_MAX_LAYERS + 2];

@@ -61,7 +61,7 @@ extern "C" int mlswlbm_diagnostics_noalloc(const mlsw_params* p, const float* f,
   if (g_setup_err[dev] != cudaSuccess || !g_scratch_ptr[dev]) return MLSW_ERR_CUDA;
   // every block writes its own partials, so nothing needs clearing first
   const cudaError_t e =
-      mlsw::launch_diagnostics(p->lattice, n, ncell, f, sh, g_scratch_ptr[dev], (int)nblk, out,
-                               (cudaStream_t)stream);
+      mlsw::launch_diagnostics(p->lattice, n, mlsw::dense_layout(p->nx, p->ny), f, sh,
+                               g_scratch_ptr[dev], (int)nblk, out, (cudaStream_t)stream);
   return e == cudaSuccess ? MLSW_OK : MLSW_ERR_CUDA;
 }

@@ -21,6 +21,25 @@ constexpr int kMaxLayers = 5;
 // storing f_0 itself loses the capillary signal; the shift keeps ~1e-10.
 // The arithmetic of the scheme is unchanged: only the representation of
 // f_0 moves by a constant.
+// Device layout of a population buffer: every plane (layer i, direction k,
+// plane index i * Q + k) is a padded 2-D array of `rows` rows of `pitch`
+// floats; the real cell (x, y) sits at row y + gy, column x + gx. The ring
+// of ghost cells within two cells of the real domain (x in [-2, nx + 2),
+// y in [-2, ny + 2) for D2Q9; x only for D1Q3) holds the periodic images of
+// the real cells, so the step kernels read a tile plus its halo without
+// any wrap-around arithmetic. gx = 4 keeps every tile's box 16-byte aligned
+// for the tensor-memory-access unit; pitch and rows cover whole tiles.
+struct Layout {
+  int nx, ny;    // real lattice
+  int gx, gy;    // padded position of the real cell (0, 0)
+  int pitch;     // floats per padded row (multiple of 4)
+  int rows;      // padded rows per plane
+  long plane;    // pitch * rows
+  __host__ __device__ long at(int p, int x, int y) const {
+    return (long)p * plane + (long)(y + gy) * pitch + (x + gx);
+  }
+};
+
 struct KParams {
   int n;
   int nx, ny;
@@ -34,6 +53,13 @@ struct KParams {
   float c_phi;                       // 1 / (nw - mw)
   float c_dphi;                      // nw mw / (nw - mw)
   float H[kMaxLayers];               // rest-population shift of each layer
+  Layout L;                          // padded layout of both population buffers
+  // periodic images: ghost column gcol[g] (g = 0..3 for x = -2, -1, nx,
+  // nx + 1) holds real column gsrcx[g]; likewise rows
+  int gsrcx[4], gsrcy[4];
+  // 1 when a side of the lattice is shorter than 4 cells: a real column or
+  // row can then have several ghost images
+  int tiny;
 };
 
 // ---------------------------------------------------------------------------
@@ -67,6 +93,23 @@ __device__ __forceinline__ float ipow(float r, int e) {
   return a;
 }
 
+// fast reciprocal: the __fdividef intrinsic (at most 2 ulp for the O(1e-2 ..
+// 1e2) arguments used here: layer thicknesses, fluxes' pivots)
+__device__ __forceinline__ float rcp(float x) { return __fdividef(1.f, x); }
+
+// r^mw and r^nw: the common exponent pair (3, 2) at compile time (W32), any
+// other pair with a run-time loop
+template <bool W32>
+__device__ __forceinline__ void wet_powers(const KParams& P, float r, float& rm, float& rn) {
+  if (W32) {
+    rm = r * r;
+    rn = rm * r;
+  } else {
+    rm = ipow(r, P.mw);
+    rn = ipow(r, P.nw);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Layer pressures p_i - p_atm at one cell (Eqs. Laplace_pressure,
 // disjoining_pressure; p_i = sum_{j>=i} (Lambda_j + Pi_j)).
@@ -76,7 +119,7 @@ __device__ __forceinline__ float ipow(float r, int e) {
 // Pi_l and added to Pi_m, and S_lk phi_k(d) raises the tension of interface
 // l. l = 0 is the flat substrate (grad z_0 = 0, no pressure of its own).
 // ---------------------------------------------------------------------------
-template <int N>
+template <int N, bool W32 = false>
 __device__ __forceinline__ void layer_pressures(const KParams& P, const float (&h)[N],
                                                 const float (&gx)[N], const float (&gy)[N],
                                                 const float (&lz)[N], float (&p)[N]) {
@@ -97,10 +140,11 @@ __device__ __forceinline__ void layer_pressures(const KParams& P, const float (&
       const int k = m - l;
       const float s = P.S[l][k - 1];
       if (s != 0.f) {
-        const float inv_d = 1.f / d;
+        const float inv_d = rcp(d);
         const float r = (float)k * P.hstar * inv_d;
-        const float rm = ipow(r, P.mw), rn = ipow(r, P.nw);
-        const float phi = ((float)P.nw * rm - (float)P.mw * rn) * P.c_phi;
+        float rm, rn;
+        wet_powers<W32>(P, r, rm, rn);
+        const float phi = W32 ? (3.f * rm - 2.f * rn) : ((float)P.nw * rm - (float)P.mw * rn) * P.c_phi;
         const float dphi = P.c_dphi * (rn - rm) * inv_d;
         const float e = s * dphi * sgl;
         if (l >= 1) {
@@ -132,10 +176,43 @@ __device__ __forceinline__ void layer_pressures(const KParams& P, const float (&
 // layer (Eq. flux) gives J = L G with an N x N matrix L built column by
 // column in O(N^2). Force balance of the thin-sheet equation,
 // 0 = -h_i G_i + 2 mu_i h_i a_i, then gives the friction R_i = h_i G_i with
-// G = L^-1 J: one factorisation, two right-hand sides (x and y).
-// L is not symmetric in general (the slip convention breaks reciprocity), so
-// the elimination pivots by rows.
+// G = L^-1 J: one factorisation, two right-hand sides (x and y), by the
+// adjugate for N <= 3 and by elimination with row pivoting for N = 4, 5 (L is
+// not symmetric in general: the slip convention breaks reciprocity).
 // ---------------------------------------------------------------------------
+// Solves L G = J for two right-hand sides with the adjugate of L
+// (N = 1, 2, 3). Unused for larger N.
+template <int N>
+__device__ __forceinline__ void solve_small(const float (&L)[N][N], const float (&Jx)[N],
+                                            const float (&Jy)[N], float (&Gx)[N],
+                                            float (&Gy)[N]) {
+  if constexpr (N == 1) {
+    const float r = rcp(L[0][0]);
+    Gx[0] = Jx[0] * r;
+    Gy[0] = Jy[0] * r;
+  } else if constexpr (N == 2) {
+    const float r = rcp(L[0][0] * L[1][1] - L[0][1] * L[1][0]);
+    Gx[0] = (L[1][1] * Jx[0] - L[0][1] * Jx[1]) * r;
+    Gx[1] = (L[0][0] * Jx[1] - L[1][0] * Jx[0]) * r;
+    Gy[0] = (L[1][1] * Jy[0] - L[0][1] * Jy[1]) * r;
+    Gy[1] = (L[0][0] * Jy[1] - L[1][0] * Jy[0]) * r;
+  } else if constexpr (N == 3) {
+    const float a = L[0][0], b = L[0][1], c = L[0][2];
+    const float d = L[1][0], e = L[1][1], f = L[1][2];
+    const float g = L[2][0], hh = L[2][1], k = L[2][2];
+    const float A00 = e * k - f * hh, A01 = c * hh - b * k, A02 = b * f - c * e;
+    const float A10 = f * g - d * k, A11 = a * k - c * g, A12 = c * d - a * f;
+    const float A20 = d * hh - e * g, A21 = b * g - a * hh, A22 = a * e - b * d;
+    const float r = rcp(a * A00 + b * A10 + c * A20);
+    Gx[0] = (A00 * Jx[0] + A01 * Jx[1] + A02 * Jx[2]) * r;
+    Gx[1] = (A10 * Jx[0] + A11 * Jx[1] + A12 * Jx[2]) * r;
+    Gx[2] = (A20 * Jx[0] + A21 * Jx[1] + A22 * Jx[2]) * r;
+    Gy[0] = (A00 * Jy[0] + A01 * Jy[1] + A02 * Jy[2]) * r;
+    Gy[1] = (A10 * Jy[0] + A11 * Jy[1] + A12 * Jy[2]) * r;
+    Gy[2] = (A20 * Jy[0] + A21 * Jy[1] + A22 * Jy[2]) * r;
+  }
+}
+
 template <int N>
 __device__ __forceinline__ void friction(const KParams& P, const float (&h)[N],
                                          const float (&Jx)[N], const float (&Jy)[N],
@@ -153,6 +230,17 @@ __device__ __forceinline__ void friction(const KParams& P, const float (&h)[N],
       L[i][j] = hi * ub + mi * hi * hi * (0.5f * s - g * (1.f / 3.f) * hi);
       ub += mi * hi * (s - 0.5f * g * hi);
     }
+  }
+  if constexpr (N <= 3) {
+    // adjugate (Cramer) solution of the 1x1 / 2x2 / 3x3 system
+    float Gx[N], Gy[N];
+    solve_small<N>(L, Jx, Jy, Gx, Gy);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      Rx[i] = h[i] * Gx[i];
+      Ry[i] = h[i] * Gy[i];
+    }
+    return;
   }
   float bx[N], by[N];
 #pragma unroll
@@ -190,7 +278,7 @@ __device__ __forceinline__ void friction(const KParams& P, const float (&h)[N],
         by[r] = t;
       }
     }
-    inv_piv[c] = 1.f / L[c][c];
+    inv_piv[c] = rcp(L[c][c]);
 #pragma unroll
     for (int r = c + 1; r < N; ++r) {
       const float l = L[r][c] * inv_piv[c];

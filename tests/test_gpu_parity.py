@@ -240,4 +240,4 @@ def test_torch_stream_binding_and_launch_count():
         a.step(40)
         b.step(40)
         assert np.array_equal(a.get_heights(), b.get_heights())
-        assert a.launch_count() == 1 + 40 + 1  # init, steps, height read-out
+        assert a.launch_count() == 2 + 40 + 1  # init + ghost images, steps, read-out
