@@ -240,6 +240,13 @@ void set_shift(mlsw_handle* h, const float* H) {
     h->sh.H[i] = v;
     h->kp.H[i] = v;
   }
+  // reference thickness between interfaces l < m, summed in double
+  for (int l = 0; l <= mlsw::kMaxLayers; ++l)
+    for (int m = 0; m <= mlsw::kMaxLayers; ++m) {
+      double acc = 0.0;
+      for (int j = l + 1; j <= m; ++j) acc += (double)h->sh.H[j - 1];
+      h->kp.Hsum[l][m] = (float)acc;
+    }
 }
 
 }  // namespace
@@ -439,8 +446,15 @@ int mlswlbm_step(mlsw_handle* h, long nsteps) {
     a.fout = h->f[h->cur ^ 1];
     a.fin_map = &h->map[h->cur];
     CU(mlsw::launch_step(a, h->stream));
-    h->cur ^= 1;
     h->launches += 1;
+    if (h->kp.tiny) {
+      // a side below 4 cells: a real cell can have several ghost images,
+      // which a separate pass refreshes
+      CU(mlsw::launch_fill_ghosts(h->p.n_layers * h->Q, h->kp.L, h->p.lattice == MLSW_D2Q9,
+                                  a.fout, h->stream));
+      h->launches += 1;
+    }
+    h->cur ^= 1;
   }
   return MLSW_OK;
 }

@@ -53,6 +53,9 @@ struct KParams {
   float c_phi;                       // 1 / (nw - mw)
   float c_dphi;                      // nw mw / (nw - mw)
   float H[kMaxLayers];               // rest-population shift of each layer
+  // Hsum[l][m] = H_{l+1} + ... + H_m (1-based layers, 0 <= l < m <= n): the
+  // reference part of the thickness z_m - z_l between interfaces l and m
+  float Hsum[kMaxLayers + 1][kMaxLayers + 1];
   Layout L;                          // padded layout of both population buffers
   // periodic images: ghost column gcol[g] (g = 0..3 for x = -2, -1, nx,
   // nx + 1) holds real column gsrcx[g]; likewise rows
@@ -87,20 +90,63 @@ template <> struct Lattice<2> {  // D2Q9, counter-clockwise from +x
   }
 };
 
-__device__ __forceinline__ float ipow(float r, int e) {
-  float a = 1.f;
-  for (int i = 0; i < e; ++i) a *= r;
+// ---------------------------------------------------------------------------
+// Arithmetic on one cell (float) or on two cells at once (f2, a packed pair
+// evaluated with the FP32x2 instructions of sm_100-class GPUs: one FFMA2 /
+// FADD2 / FMUL2 does the work of two scalar ones). The per-cell routines
+// below are written once over T in {float, f2}.
+// ---------------------------------------------------------------------------
+struct f2 {
+  float2 v;
+};
+__device__ __forceinline__ f2 mk2(float a, float b) { return {make_float2(a, b)}; }
+__device__ __forceinline__ f2 operator+(f2 a, f2 b) { return {__fadd2_rn(a.v, b.v)}; }
+__device__ __forceinline__ f2 operator*(f2 a, f2 b) { return {__fmul2_rn(a.v, b.v)}; }
+// a - b as one FFMA2: b * (-1) + a (exact product, one rounding)
+__device__ __forceinline__ f2 operator-(f2 a, f2 b) {
+  return {__ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v)};
+}
+__device__ __forceinline__ f2 operator-(f2 a) { return {make_float2(-a.v.x, -a.v.y)}; }
+__device__ __forceinline__ f2 operator+(f2 a, float b) { return a + mk2(b, b); }
+__device__ __forceinline__ f2 operator+(float a, f2 b) { return mk2(a, a) + b; }
+__device__ __forceinline__ f2 operator-(f2 a, float b) { return a - mk2(b, b); }
+__device__ __forceinline__ f2 operator-(float a, f2 b) { return mk2(a, a) - b; }
+__device__ __forceinline__ f2 operator*(f2 a, float b) { return a * mk2(b, b); }
+__device__ __forceinline__ f2 operator*(float a, f2 b) { return mk2(a, a) * b; }
+__device__ __forceinline__ f2& operator+=(f2& a, f2 b) { return a = a + b; }
+__device__ __forceinline__ f2& operator-=(f2& a, f2 b) { return a = a - b; }
+
+template <class T> struct Num;
+template <> struct Num<float> {
+  __device__ static float splat(float a) { return a; }
+};
+template <> struct Num<f2> {
+  __device__ static f2 splat(float a) { return mk2(a, a); }
+};
+
+__device__ __forceinline__ float fmav(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ f2 fmav(f2 a, f2 b, f2 c) { return {__ffma2_rn(a.v, b.v, c.v)}; }
+__device__ __forceinline__ f2 fmav(f2 a, float b, f2 c) { return fmav(a, mk2(b, b), c); }
+__device__ __forceinline__ f2 fmav(float a, f2 b, f2 c) { return fmav(mk2(a, a), b, c); }
+__device__ __forceinline__ f2 fmav(f2 a, f2 b, float c) { return fmav(a, b, mk2(c, c)); }
+__device__ __forceinline__ f2 fmav(f2 a, float b, float c) { return fmav(a, mk2(b, b), mk2(c, c)); }
+
+// fast reciprocal: the __fdividef intrinsic (at most 2 ulp for the O(1e-2 ..
+// 1e2) arguments used here: layer thicknesses, friction pivots)
+__device__ __forceinline__ float rcp(float x) { return __fdividef(1.f, x); }
+__device__ __forceinline__ f2 rcp(f2 x) { return mk2(rcp(x.v.x), rcp(x.v.y)); }
+
+template <class T>
+__device__ __forceinline__ T ipow(T r, int e) {
+  T a = Num<T>::splat(1.f);
+  for (int i = 0; i < e; ++i) a = a * r;
   return a;
 }
 
-// fast reciprocal: the __fdividef intrinsic (at most 2 ulp for the O(1e-2 ..
-// 1e2) arguments used here: layer thicknesses, fluxes' pivots)
-__device__ __forceinline__ float rcp(float x) { return __fdividef(1.f, x); }
-
 // r^mw and r^nw: the common exponent pair (3, 2) at compile time (W32), any
 // other pair with a run-time loop
-template <bool W32>
-__device__ __forceinline__ void wet_powers(const KParams& P, float r, float& rm, float& rn) {
+template <bool W32, class T>
+__device__ __forceinline__ void wet_powers(const KParams& P, T r, T& rm, T& rn) {
   if (W32) {
     rm = r * r;
     rn = rm * r;
@@ -113,52 +159,62 @@ __device__ __forceinline__ void wet_powers(const KParams& P, float r, float& rm,
 // ---------------------------------------------------------------------------
 // Layer pressures p_i - p_atm at one cell (Eqs. Laplace_pressure,
 // disjoining_pressure; p_i = sum_{j>=i} (Lambda_j + Pi_j)).
-// Every interface pair (l, m = l + k), 0 <= l < m <= N, enters once:
-// thickness d = z_m - z_l = h_{l+1} + ... + h_m (summed from h, no
-// cancellation), E = S_lk phi'_k(d) (1 + |grad z_l|^2 / 2) is subtracted from
-// Pi_l and added to Pi_m, and S_lk phi_k(d) raises the tension of interface
-// l. l = 0 is the flat substrate (grad z_0 = 0, no pressure of its own).
+// Every interface pair (l, m = l + k), 0 <= l < m <= N, enters once with
+// the thickness d = z_m - z_l between them: E = S_lk phi'_k(d)
+// (1 + |grad z_l|^2 / 2) is subtracted from Pi_l and added to Pi_m, and
+// S_lk phi_k(d) raises the tension of interface l. l = 0 is the flat
+// substrate (grad z_0 = 0, no pressure of its own).
+// The inputs are the deviations of the interface heights, zd[i - 1] =
+// z_i - (H_1 + ... + H_i), so d = Hsum[l][m] + (zd_m - zd_l) (zd_0 = 0): the
+// deviations are O(1e-3) numbers and their differences carry the FP32
+// round-off of the deviations, not of the O(1) heights.
 // ---------------------------------------------------------------------------
-template <int N, bool W32 = false>
-__device__ __forceinline__ void layer_pressures(const KParams& P, const float (&h)[N],
-                                                const float (&gx)[N], const float (&gy)[N],
-                                                const float (&lz)[N], float (&p)[N]) {
-  float ten[N], pi[N], sg[N];
+// NN: only nearest-neighbour pairs (k = 1) carry a spreading coefficient
+// (S_{lk} = 0 for k >= 2, as in the paper's three-layer runs); the pair loop
+// is then branch-free.
+template <int N, bool W32, class T, bool NN = false>
+__device__ __forceinline__ void layer_pressures_dev(const KParams& P, const T (&zd)[N],
+                                                    const T (&gx)[N], const T (&gy)[N],
+                                                    const T (&lz)[N], T (&p)[N]) {
+  T ten[N], pi[N], sg[N];
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    ten[i] = P.gamma[i];
-    pi[i] = 0.f;
-    sg[i] = 1.f + 0.5f * (gx[i] * gx[i] + gy[i] * gy[i]);
+    ten[i] = Num<T>::splat(P.gamma[i]);
+    pi[i] = Num<T>::splat(0.f);
+    sg[i] = fmav(0.5f, fmav(gx[i], gx[i], gy[i] * gy[i]), Num<T>::splat(1.f));
   }
 #pragma unroll
   for (int l = 0; l < N; ++l) {
-    const float sgl = (l == 0) ? 1.f : sg[l > 0 ? l - 1 : 0];
-    float d = 0.f;
+    const T sgl = (l == 0) ? Num<T>::splat(1.f) : sg[l > 0 ? l - 1 : 0];
+    const T zl = (l == 0) ? Num<T>::splat(0.f) : zd[l > 0 ? l - 1 : 0];
 #pragma unroll
-    for (int m = l + 1; m <= N; ++m) {
-      d += h[m - 1];
+    for (int m = l + 1; m <= (NN ? l + 1 : N); ++m) {
       const int k = m - l;
       const float s = P.S[l][k - 1];
-      if (s != 0.f) {
-        const float inv_d = rcp(d);
-        const float r = (float)k * P.hstar * inv_d;
-        float rm, rn;
+      if (NN || s != 0.f) {
+        const T d = (zd[m - 1] - zl) + P.Hsum[l][m];
+        const T inv_d = rcp(d);
+        const T r = ((float)k * P.hstar) * inv_d;
+        T rm, rn;
         wet_powers<W32>(P, r, rm, rn);
-        const float phi = W32 ? (3.f * rm - 2.f * rn) : ((float)P.nw * rm - (float)P.mw * rn) * P.c_phi;
-        const float dphi = P.c_dphi * (rn - rm) * inv_d;
-        const float e = s * dphi * sgl;
+        const T phi = W32 ? fmav(rm, 3.f, -2.f * rn)
+                          : (fmav(rm, (float)P.nw, -(float)P.mw * rn)) * P.c_phi;
+        const T dphi = (P.c_dphi * (rn - rm)) * inv_d;
+        const T se = s * dphi;
+        // explicit fused updates, so one cell and a packed pair of cells
+        // round identically
         if (l >= 1) {
-          ten[l > 0 ? l - 1 : 0] += s * phi;
-          pi[l > 0 ? l - 1 : 0] -= e;
+          ten[l > 0 ? l - 1 : 0] = fmav(s, phi, ten[l > 0 ? l - 1 : 0]);
+          pi[l > 0 ? l - 1 : 0] = fmav(-se, sgl, pi[l > 0 ? l - 1 : 0]);
         }
-        pi[m - 1] += e;
+        pi[m - 1] = fmav(se, sgl, pi[m - 1]);
       }
     }
   }
-  float acc = 0.f;
+  T acc = Num<T>::splat(0.f);
 #pragma unroll
   for (int i = N - 1; i >= 0; --i) {
-    acc += pi[i] - ten[i] * lz[i];
+    acc = acc + fmav(-ten[i], lz[i], pi[i]);
     p[i] = acc;
   }
 }
@@ -178,62 +234,71 @@ __device__ __forceinline__ void layer_pressures(const KParams& P, const float (&
 // 0 = -h_i G_i + 2 mu_i h_i a_i, then gives the friction R_i = h_i G_i with
 // G = L^-1 J: one factorisation, two right-hand sides (x and y), by the
 // adjugate for N <= 3 and by elimination with row pivoting for N = 4, 5 (L is
-// not symmetric in general: the slip convention breaks reciprocity).
+// not symmetric in general: the slip convention breaks reciprocity; the
+// pivoted form is scalar only).
 // ---------------------------------------------------------------------------
 // Solves L G = J for two right-hand sides with the adjugate of L
 // (N = 1, 2, 3). Unused for larger N.
-template <int N>
-__device__ __forceinline__ void solve_small(const float (&L)[N][N], const float (&Jx)[N],
-                                            const float (&Jy)[N], float (&Gx)[N],
-                                            float (&Gy)[N]) {
+template <int N, class T>
+__device__ __forceinline__ void solve_small(const T (&L)[N][N], const T (&Jx)[N],
+                                            const T (&Jy)[N], T (&Gx)[N], T (&Gy)[N]) {
   if constexpr (N == 1) {
-    const float r = rcp(L[0][0]);
+    const T r = rcp(L[0][0]);
     Gx[0] = Jx[0] * r;
     Gy[0] = Jy[0] * r;
   } else if constexpr (N == 2) {
-    const float r = rcp(L[0][0] * L[1][1] - L[0][1] * L[1][0]);
-    Gx[0] = (L[1][1] * Jx[0] - L[0][1] * Jx[1]) * r;
-    Gx[1] = (L[0][0] * Jx[1] - L[1][0] * Jx[0]) * r;
-    Gy[0] = (L[1][1] * Jy[0] - L[0][1] * Jy[1]) * r;
-    Gy[1] = (L[0][0] * Jy[1] - L[1][0] * Jy[0]) * r;
+    const T r = rcp(fmav(L[0][0], L[1][1], -(L[0][1] * L[1][0])));
+    Gx[0] = fmav(L[1][1], Jx[0], -(L[0][1] * Jx[1])) * r;
+    Gx[1] = fmav(L[0][0], Jx[1], -(L[1][0] * Jx[0])) * r;
+    Gy[0] = fmav(L[1][1], Jy[0], -(L[0][1] * Jy[1])) * r;
+    Gy[1] = fmav(L[0][0], Jy[1], -(L[1][0] * Jy[0])) * r;
   } else if constexpr (N == 3) {
-    const float a = L[0][0], b = L[0][1], c = L[0][2];
-    const float d = L[1][0], e = L[1][1], f = L[1][2];
-    const float g = L[2][0], hh = L[2][1], k = L[2][2];
-    const float A00 = e * k - f * hh, A01 = c * hh - b * k, A02 = b * f - c * e;
-    const float A10 = f * g - d * k, A11 = a * k - c * g, A12 = c * d - a * f;
-    const float A20 = d * hh - e * g, A21 = b * g - a * hh, A22 = a * e - b * d;
-    const float r = rcp(a * A00 + b * A10 + c * A20);
-    Gx[0] = (A00 * Jx[0] + A01 * Jx[1] + A02 * Jx[2]) * r;
-    Gx[1] = (A10 * Jx[0] + A11 * Jx[1] + A12 * Jx[2]) * r;
-    Gx[2] = (A20 * Jx[0] + A21 * Jx[1] + A22 * Jx[2]) * r;
-    Gy[0] = (A00 * Jy[0] + A01 * Jy[1] + A02 * Jy[2]) * r;
-    Gy[1] = (A10 * Jy[0] + A11 * Jy[1] + A12 * Jy[2]) * r;
-    Gy[2] = (A20 * Jy[0] + A21 * Jy[1] + A22 * Jy[2]) * r;
+    const T a = L[0][0], b = L[0][1], c = L[0][2];
+    const T d = L[1][0], e = L[1][1], f = L[1][2];
+    const T g = L[2][0], hh = L[2][1], k = L[2][2];
+    const T A00 = fmav(e, k, -(f * hh)), A01 = fmav(c, hh, -(b * k)), A02 = fmav(b, f, -(c * e));
+    const T A10 = fmav(f, g, -(d * k)), A11 = fmav(a, k, -(c * g)), A12 = fmav(c, d, -(a * f));
+    const T A20 = fmav(d, hh, -(e * g)), A21 = fmav(b, g, -(a * hh)), A22 = fmav(a, e, -(b * d));
+    const T r = rcp(fmav(a, A00, fmav(b, A10, c * A20)));
+    Gx[0] = fmav(A00, Jx[0], fmav(A01, Jx[1], A02 * Jx[2])) * r;
+    Gx[1] = fmav(A10, Jx[0], fmav(A11, Jx[1], A12 * Jx[2])) * r;
+    Gx[2] = fmav(A20, Jx[0], fmav(A21, Jx[1], A22 * Jx[2])) * r;
+    Gy[0] = fmav(A00, Jy[0], fmav(A01, Jy[1], A02 * Jy[2])) * r;
+    Gy[1] = fmav(A10, Jy[0], fmav(A11, Jy[1], A12 * Jy[2])) * r;
+    Gy[2] = fmav(A20, Jy[0], fmav(A21, Jy[1], A22 * Jy[2])) * r;
   }
 }
 
-template <int N>
-__device__ __forceinline__ void friction(const KParams& P, const float (&h)[N],
-                                         const float (&Jx)[N], const float (&Jy)[N],
-                                         float (&Rx)[N], float (&Ry)[N]) {
-  float L[N][N];
+template <int N, class T>
+__device__ __forceinline__ void friction(const KParams& P, const T (&h)[N], const T (&Jx)[N],
+                                         const T (&Jy)[N], T (&Rx)[N], T (&Ry)[N]) {
+  T L[N][N];
 #pragma unroll
   for (int j = 0; j < N; ++j) {
-    float ub = 0.f;  // velocity at the bottom of layer i for unit G_j
+    T ub = Num<T>::splat(0.f);  // velocity at the bottom of layer i for unit G_j
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      const float s = (j > i) ? -h[j] : 0.f;  // stress at z_i
-      const float g = (i == j) ? 1.f : 0.f;
-      const float mi = P.mu_inv[i], bi = P.beta[i], hi = h[i];
-      ub += bi * mi * (s - g * (hi + 0.5f * bi));
-      L[i][j] = hi * ub + mi * hi * hi * (0.5f * s - g * (1.f / 3.f) * hi);
-      ub += mi * hi * (s - 0.5f * g * hi);
+      const float mi = P.mu_inv[i], bi = P.beta[i];
+      const T hi = h[i];
+      if (j > i) {
+        // unit gradient in a layer above: only the stress s = -h_j acts
+        const T s = -h[j];
+        ub = fmav(s, bi * mi, ub);
+        L[i][j] = fmav(hi, ub, (mi * 0.5f) * (hi * hi) * s);
+        ub = fmav(mi * hi, s, ub);
+      } else if (j == i) {
+        // unit gradient in this layer (g = 1, s = 0)
+        ub = fmav(-(bi * mi), hi + 0.5f * bi, ub);
+        L[i][j] = fmav(hi, ub, (-mi / 3.f) * (hi * hi) * hi);
+        ub = fmav(-0.5f * mi, hi * hi, ub);
+      } else {
+        L[i][j] = hi * ub;  // layers above the forced one move with it
+      }
     }
   }
   if constexpr (N <= 3) {
     // adjugate (Cramer) solution of the 1x1 / 2x2 / 3x3 system
-    float Gx[N], Gy[N];
+    T Gx[N], Gy[N];
     solve_small<N>(L, Jx, Jy, Gx, Gy);
 #pragma unroll
     for (int i = 0; i < N; ++i) {
@@ -241,68 +306,70 @@ __device__ __forceinline__ void friction(const KParams& P, const float (&h)[N],
       Ry[i] = h[i] * Gy[i];
     }
     return;
-  }
-  float bx[N], by[N];
+  } else {
+    static_assert(sizeof(T) == sizeof(float), "pivoted elimination is scalar");
+    float bx[N], by[N];
 #pragma unroll
-  for (int i = 0; i < N; ++i) {
-    bx[i] = Jx[i];
-    by[i] = Jy[i];
-  }
-  float inv_piv[N];
-#pragma unroll
-  for (int c = 0; c < N; ++c) {
-    int piv = c;
-    float best = fabsf(L[c][c]);
-#pragma unroll
-    for (int r = c + 1; r < N; ++r) {
-      const float a = fabsf(L[r][c]);
-      if (a > best) {
-        best = a;
-        piv = r;
-      }
+    for (int i = 0; i < N; ++i) {
+      bx[i] = Jx[i];
+      by[i] = Jy[i];
     }
+    float inv_piv[N];
 #pragma unroll
-    for (int r = c + 1; r < N; ++r) {
-      if (piv == r) {
+    for (int c = 0; c < N; ++c) {
+      int piv = c;
+      float best = fabsf(L[c][c]);
 #pragma unroll
-        for (int q = c; q < N; ++q) {
-          const float t = L[c][q];
-          L[c][q] = L[r][q];
-          L[r][q] = t;
+      for (int r = c + 1; r < N; ++r) {
+        const float a = fabsf(L[r][c]);
+        if (a > best) {
+          best = a;
+          piv = r;
         }
-        float t = bx[c];
-        bx[c] = bx[r];
-        bx[r] = t;
-        t = by[c];
-        by[c] = by[r];
-        by[r] = t;
+      }
+#pragma unroll
+      for (int r = c + 1; r < N; ++r) {
+        if (piv == r) {
+#pragma unroll
+          for (int q = c; q < N; ++q) {
+            const float t = L[c][q];
+            L[c][q] = L[r][q];
+            L[r][q] = t;
+          }
+          float t = bx[c];
+          bx[c] = bx[r];
+          bx[r] = t;
+          t = by[c];
+          by[c] = by[r];
+          by[r] = t;
+        }
+      }
+      inv_piv[c] = rcp(L[c][c]);
+#pragma unroll
+      for (int r = c + 1; r < N; ++r) {
+        const float l = L[r][c] * inv_piv[c];
+#pragma unroll
+        for (int q = c + 1; q < N; ++q) L[r][q] -= l * L[c][q];
+        bx[r] -= l * bx[c];
+        by[r] -= l * by[c];
       }
     }
-    inv_piv[c] = rcp(L[c][c]);
 #pragma unroll
-    for (int r = c + 1; r < N; ++r) {
-      const float l = L[r][c] * inv_piv[c];
+    for (int c = N - 1; c >= 0; --c) {
+      float sx = bx[c], sy = by[c];
 #pragma unroll
-      for (int q = c + 1; q < N; ++q) L[r][q] -= l * L[c][q];
-      bx[r] -= l * bx[c];
-      by[r] -= l * by[c];
+      for (int q = c + 1; q < N; ++q) {
+        sx -= L[c][q] * bx[q];
+        sy -= L[c][q] * by[q];
+      }
+      bx[c] = sx * inv_piv[c];
+      by[c] = sy * inv_piv[c];
     }
-  }
 #pragma unroll
-  for (int c = N - 1; c >= 0; --c) {
-    float sx = bx[c], sy = by[c];
-#pragma unroll
-    for (int q = c + 1; q < N; ++q) {
-      sx -= L[c][q] * bx[q];
-      sy -= L[c][q] * by[q];
+    for (int i = 0; i < N; ++i) {
+      Rx[i] = h[i] * bx[i];
+      Ry[i] = h[i] * by[i];
     }
-    bx[c] = sx * inv_piv[c];
-    by[c] = sy * inv_piv[c];
-  }
-#pragma unroll
-  for (int i = 0; i < N; ++i) {
-    Rx[i] = h[i] * bx[i];
-    Ry[i] = h[i] * by[i];
   }
 }
 

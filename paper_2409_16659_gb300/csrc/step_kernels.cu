@@ -25,6 +25,8 @@
 // on an mbarrier; each CTA refills its stage with the next tile as soon as
 // the moments of the current one are formed, so copies overlap arithmetic.
 // D1Q3 (small 1-D lattices) uses a plain tiled kernel.
+#include <type_traits>
+
 #include "kernels.h"
 #include "physics.cuh"
 #include "tma.cuh"
@@ -33,36 +35,8 @@ namespace mlsw {
 
 // ---------------------------------------------------------------------------
 // Stores of one post-collision population to its streamed destination
-// (dx, dy) (already periodic) and to every ghost cell that images it.
-// xm / ym: bit g set when ghost column / row g (x = -2, -1, nx, nx + 1)
-// images the destination column / row.
+// (dx, dy) (already periodic) and to the ghost cells that image it.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int ghost_pos(int g, int n) {
-  return g == 0 ? -2 : (g == 1 ? -1 : (g == 2 ? n : n + 1));
-}
-
-__device__ __forceinline__ unsigned ghost_mask(const int (&src)[4], int d) {
-  return (src[0] == d ? 1u : 0u) | (src[1] == d ? 2u : 0u) | (src[2] == d ? 4u : 0u) |
-         (src[3] == d ? 8u : 0u);
-}
-
-__device__ __forceinline__ void store_images(float* __restrict__ plane_base, const Layout& L,
-                                             int dx, int dy, unsigned xm, unsigned ym, float v) {
-  plane_base[(long)(dy + L.gy) * L.pitch + dx + L.gx] = v;
-  if (xm | ym) {
-    for (int gr = -1; gr < 4; ++gr) {
-      if (gr >= 0 && !((ym >> gr) & 1u)) continue;
-      const int yy = gr < 0 ? dy : ghost_pos(gr, L.ny);
-      for (int gc = -1; gc < 4; ++gc) {
-        if (gr < 0 && gc < 0) continue;
-        if (gc >= 0 && !((xm >> gc) & 1u)) continue;
-        const int xx = gc < 0 ? dx : ghost_pos(gc, L.nx);
-        plane_base[(long)(yy + L.gy) * L.pitch + xx + L.gx] = v;
-      }
-    }
-  }
-}
-
 // Lattices with both sides >= 4 cells: a real column d has at most one
 // ghost image (d + n for d < 2, d - n for d >= n - 2), likewise rows, so a
 // population near an edge needs at most three extra stores.
@@ -120,49 +94,73 @@ __device__ __forceinline__ void collide(const KParams& P, float h, float dh, flo
 // one symmetric and one antisymmetric part. Directions: 1 (1,0), 2 (1,1),
 // 3 (0,1), 4 (-1,1); 5..8 are their opposites.
 // ---------------------------------------------------------------------------
-template <bool TAU1>
-__device__ __forceinline__ void collide_d2q9(const KParams& P, float h, float dh, float jx,
-                                             float jy, float Fx, float Fy, const float* f_old,
-                                             float (&fs)[9]) {
-  const float ih = rcp(h);
-  const float ux = jx * ih, uy = jy * ih;
-  const float u15 = 1.5f * (ux * ux + uy * uy);
-  float sumsym = 0.f;
-  const float cus[4] = {ux, ux + uy, uy, uy - ux};
-  const float cfs[4] = {Fx, Fx + Fy, Fy, Fy - Fx};
+template <bool TAU1, class T>
+__device__ __forceinline__ void collide_d2q9(const KParams& P, T h, T dh, T jx, T jy, T Fx, T Fy,
+                                             const T* f_old, T (&fs)[9]) {
+  const T ih = rcp(h);
+  const T ux = jx * ih, uy = jy * ih;
+  const T u15 = 1.5f * fmav(ux, ux, uy * uy);
+  T sumsym = Num<T>::splat(0.f);
+  const T cus[4] = {ux, ux + uy, uy, uy - ux};
+  const T cfs[4] = {Fx, Fx + Fy, Fy, Fy - Fx};
   const float ws[4] = {1.f / 9.f, 1.f / 36.f, 1.f / 9.f, 1.f / 36.f};
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    const float A = ws[q] * h;
-    const float cu = cus[q];
-    const float sym = A * (4.5f * cu * cu - u15);
+    const T A = ws[q] * h;
+    const T cu = cus[q];
+    const T sym = A * fmav(4.5f * cu, cu, -u15);
     sumsym += sym;
-    if (TAU1) {
-      const float anti = 3.f * (A * cu + ws[q] * cfs[q]);
+    if constexpr (TAU1) {
+      const T anti = 3.f * fmav(A, cu, ws[q] * cfs[q]);
       fs[q + 1] = sym + anti;
       fs[q + 5] = sym - anti;
     } else {
-      const float aeq = 3.f * A * cu, afr = 3.f * ws[q] * cfs[q];
-      fs[q + 1] = f_old[q + 1] + P.omega * ((sym + aeq) - f_old[q + 1]) + afr;
-      fs[q + 5] = f_old[q + 5] + P.omega * ((sym - aeq) - f_old[q + 5]) - afr;
+      const T aeq = (3.f * A) * cu, afr = (3.f * ws[q]) * cfs[q];
+      fs[q + 1] = fmav(P.omega, (sym + aeq) - f_old[q + 1], f_old[q + 1]) + afr;
+      fs[q + 5] = fmav(P.omega, (sym - aeq) - f_old[q + 5], f_old[q + 5]) - afr;
     }
   }
   // rest population h - (sum of moving equilibria) = h (1 - w_0 U^2/(2 cs^2)),
   // stored shifted by H
-  const float geq0 = dh - 2.f * sumsym;
-  fs[0] = TAU1 ? geq0 : f_old[0] + P.omega * (geq0 - f_old[0]);
+  const T geq0 = fmav(-2.f, sumsym, dh);
+  if constexpr (TAU1)
+    fs[0] = geq0;
+  else
+    fs[0] = fmav(P.omega, geq0 - f_old[0], f_old[0]);
 }
 
+// Loads / stores of one cell (float) or of a pair of cells (f2) at two
+// addresses.
+template <class T> struct Lanes;
+template <> struct Lanes<float> {
+  static constexpr int W = 1;
+  __device__ static float ld(const float* a, const float*) { return *a; }
+  __device__ static void st(float* a, float*, float v) { *a = v; }
+  __device__ static float get(float v, int) { return v; }
+};
+template <> struct Lanes<f2> {
+  static constexpr int W = 2;
+  __device__ static f2 ld(const float* a, const float* b) { return mk2(*a, *b); }
+  __device__ static void st(float* a, float* b, f2 v) {
+    *a = v.v.x;
+    *b = v.v.y;
+  }
+  __device__ static float get(f2 v, int l) { return l ? v.v.y : v.v.x; }
+};
+
 // ---------------------------------------------------------------------------
-// D2Q9, persistent, TMA-fed. Tile 32 x TY, NT threads (32 x BY), RPT tile
+// D2Q9, persistent, TMA-fed. Tile 32 x TY, 256 threads (32 x 8), RPT tile
 // rows per thread. Shared memory (floats unless noted):
 //   stage [9N][TY + 4][40]   TMA box, x from x0 - 4, y from y0 - 2
-//   zs, hs [N][TY + 4][36]   z_i deviation / h_i on the two-ring region
-//   ps     [N][TY + 2][34]   p_i on the one-ring region
+//   zs    [N][TY + 4][36]    interface-height deviations z_i - sum_{j<=i} H_j
+//                            on the two-ring region (their differences give
+//                            the layer thicknesses)
+//   ps    [N][TY + 2][34]    p_i on the one-ring region
+//   js    [2][N][TY][32]     fluxes J_i of the tile cells
 //   bar                      mbarrier (8 bytes)
-// Each CTA needs about 111 KB, so two CTAs share an SM and fill each
-// other's barrier waits. With tau = 1 the next tile's copy is issued as soon
-// as the moments are formed and lands while this tile finishes.
+// About 112 KB per CTA, so two CTAs share an SM and fill each other's
+// barrier waits. With tau = 1 the next tile's copy is issued as soon as the
+// moments are formed and lands while this tile is finished.
 // ---------------------------------------------------------------------------
 template <int N>
 struct D2Tile {
@@ -173,28 +171,40 @@ struct D2Tile {
   static constexpr int NHALO = 4 * RW + 4 * TY;
   static constexpr size_t kStageBytes = (size_t)STAGE * 4;
   static constexpr size_t kOffZ = kStageBytes;
-  static constexpr size_t kOffH = kOffZ + (size_t)N * RH * RW * 4;
-  static constexpr size_t kOffP = kOffH + (size_t)N * RH * RW * 4;
-  static constexpr size_t kOffBar = (kOffP + (size_t)N * PH * PW * 4 + 15) / 16 * 16;
+  static constexpr size_t kOffP = kOffZ + (size_t)N * RH * RW * 4;
+  static constexpr size_t kOffJ = kOffP + (size_t)N * PH * PW * 4;
+  static constexpr size_t kOffBar = (kOffJ + (size_t)2 * N * TY * TX * 4 + 15) / 16 * 16;
   static constexpr size_t kSmem = kOffBar + 16;
   static_assert(kStageBytes % 128 == 0, "stage alignment");
   static_assert(NHALO <= NT, "one halo cell per thread");
   static_assert(RPT * BY == TY, "tile rows");
+  static_assert(kSmem <= 115712, "two CTAs per SM");
 };
 
-template <int N, bool TAU1, bool W32>
+// Kernel modes: the general step for tau != 1 and for tau = 1, and a fast
+// step for the case the paper runs (tau = 1, wetting exponents (3, 2),
+// spreading coefficients only between neighbouring interfaces).
+enum StepMode { kGeneral = 0, kTau1 = 1, kFast = 2 };
+
+template <int N, int MODE>
 __global__ void __launch_bounds__(256, 2)
     step_d2q9_tma(const __grid_constant__ CUtensorMap fin_map, float* __restrict__ fout,
                   const KParams P, int* __restrict__ status, int* __restrict__ sched) {
-  using T = D2Tile<N>;
-  constexpr int Q = 9, TX = T::TX, TY = T::TY, BY = T::BY, RPT = T::RPT;
-  constexpr int BW = T::BW, BH = T::BH, RW = T::RW, RH = T::RH, PW = T::PW, PH = T::PH;
+  constexpr bool TAU1 = MODE != kGeneral, W32 = MODE == kFast, NN = MODE == kFast;
+  using Tl = D2Tile<N>;
+  constexpr int Q = 9, TX = Tl::TX, TY = Tl::TY, BY = Tl::BY, RPT = Tl::RPT;
+  constexpr int BW = Tl::BW, BH = Tl::BH, RW = Tl::RW, RH = Tl::RH, PW = Tl::PW, PH = Tl::PH;
+  // a thread's two tile rows (iy, iy + BY) are evaluated as one FP32x2 pair
+  using T = typename std::conditional<RPT == 2, f2, float>::type;
+  using Ln = Lanes<T>;
+  constexpr int W = Ln::W;
+  static_assert(RPT == W, "one lane per tile row of the thread");
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   float* stage = reinterpret_cast<float*>(smem_raw);
-  float* zs = reinterpret_cast<float*>(smem_raw + T::kOffZ);
-  float* hs = reinterpret_cast<float*>(smem_raw + T::kOffH);
-  float* ps = reinterpret_cast<float*>(smem_raw + T::kOffP);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + T::kOffBar);
+  float* zs = reinterpret_cast<float*>(smem_raw + Tl::kOffZ);
+  float* ps = reinterpret_cast<float*>(smem_raw + Tl::kOffP);
+  float* js = reinterpret_cast<float*>(smem_raw + Tl::kOffJ);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + Tl::kOffBar);
   __shared__ int next_tile;
 
   const int tid = threadIdx.x;
@@ -205,9 +215,30 @@ __global__ void __launch_bounds__(256, 2)
   auto issue = [&](int t) {
     const int bx = t % ntx, by = t / ntx;
     fence_proxy_async_smem();
-    mbar_arrive_expect_tx(bar, (uint32_t)T::kStageBytes);
+    mbar_arrive_expect_tx(bar, (uint32_t)Tl::kStageBytes);
     // box origin: real (x0 - 4, y0 - 2) = padded (x0, y0) since gx = 4, gy = 2
     tma_load_3d(stage, &fin_map, bar, bx * TX, by * TY, 0);
+  };
+  auto draw_next = [&]() {
+    const int nt = (int)gridDim.x + atomicAdd(sched, 1);
+    next_tile = nt;
+    if (nt < ntiles) issue(nt);
+  };
+  // two-ring cell of halo index q (the ring around the tile)
+  auto halo_cell = [&](int q, int& r, int& c) {
+    if (q < 2 * RW) {
+      r = q / RW;
+      c = q - r * RW;
+    } else if (q < 4 * RW) {
+      const int u = q - 2 * RW;
+      r = RH - 2 + u / RW;
+      c = u % RW;
+    } else {
+      const int u = q - 4 * RW;
+      r = 2 + (u >> 2);
+      const int c4 = u & 3;
+      c = c4 < 2 ? c4 : RW - 4 + c4;
+    }
   };
 
   if (tid == 0) {
@@ -220,7 +251,7 @@ __global__ void __launch_bounds__(256, 2)
     if ((int)blockIdx.x < ntiles) issue(blockIdx.x);
   }
 
-  const int ix = tid % TX, iyb = tid / TX;  // tile cells (ix, iyb + r * BY)
+  const int ix = tid % TX, iyb = tid / TX;  // tile cells (ix, iyb + lane * BY)
   const long lplane = (long)Q * L.plane;    // floats per layer
   bool bad = false;
   uint32_t parity = 0;
@@ -231,67 +262,40 @@ __global__ void __launch_bounds__(256, 2)
     const bool timed_out = !mbar_wait_bounded(bar, parity);
     const int x0 = (t % ntx) * TX, y0 = (t / ntx) * TY;
 
-    // ---- M. moments -------------------------------------------------------
-    float hh[RPT][N], dd[RPT][N], jx[RPT][N], jy[RPT][N];
-#pragma unroll
-    for (int rr = 0; rr < RPT; ++rr) {
-      const int r = iyb + rr * BY + 2, c = ix + 2;  // two-ring coordinates
-      const float* src = stage + r * BW + (c + 2);  // stage column = c + 2
-      float z = 0.f;
+    // ---- M. moments: deviations z on the two-ring region, J on the tile ----
+    {
+      const int rA = iyb + 2, rB = iyb + (W - 1) * BY + 2, c = ix + 2;  // two-ring coords
+      const float* sA = stage + rA * BW + (c + 2);  // stage column = c + 2
+      const float* sB = stage + rB * BW + (c + 2);
+      T z = Num<T>::splat(0.f);
 #pragma unroll
       for (int i = 0; i < N; ++i) {
-        float v[Q];
+        T v[Q];
 #pragma unroll
-        for (int k = 0; k < Q; ++k) v[k] = src[(i * Q + k) * BH * BW];
-        const float sm = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
-        dd[rr][i] = sm;
-        hh[rr][i] = P.H[i] + sm;
-        jx[rr][i] = ((v[1] + v[2]) + v[8]) - ((v[4] + v[5]) + v[6]);
-        jy[rr][i] = ((v[2] + v[3]) + v[4]) - ((v[6] + v[7]) + v[8]);
-        z += sm;
-        zs[(i * RH + r) * RW + c] = z;
-        hs[(i * RH + r) * RW + c] = hh[rr][i];
+        for (int k = 0; k < Q; ++k) v[k] = Ln::ld(sA + (i * Q + k) * BH * BW, sB + (i * Q + k) * BH * BW);
+        z += ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
+        Ln::st(zs + (i * RH + rA) * RW + c, zs + (i * RH + rB) * RW + c, z);
+        Ln::st(js + ((0 * N + i) * TY + rA - 2) * TX + ix, js + ((0 * N + i) * TY + rB - 2) * TX + ix,
+               ((v[1] + v[2]) + v[8]) - ((v[4] + v[5]) + v[6]));
+        Ln::st(js + ((1 * N + i) * TY + rA - 2) * TX + ix, js + ((1 * N + i) * TY + rB - 2) * TX + ix,
+               ((v[2] + v[3]) + v[4]) - ((v[6] + v[7]) + v[8]));
       }
     }
-    if (tid < T::NHALO) {
-      const int q = tid;
+    if (tid < Tl::NHALO) {
+      // halo cells one per thread (sums only), through the same T arithmetic
+      // as the tile cells (both lanes on one cell) so every cell's z has the
+      // same bits whichever tile computes it
       int r, c;
-      if (q < 2 * RW) {
-        r = q / RW;
-        c = q - r * RW;
-      } else if (q < 4 * RW) {
-        const int u = q - 2 * RW;
-        r = RH - 2 + u / RW;
-        c = u % RW;
-      } else {
-        const int u = q - 4 * RW;
-        r = 2 + (u >> 2);
-        const int c4 = u & 3;
-        c = c4 < 2 ? c4 : RW - 4 + c4;
-      }
+      halo_cell(tid, r, c);
       const float* src = stage + r * BW + (c + 2);
-      float z = 0.f;
+      T z = Num<T>::splat(0.f);
 #pragma unroll
       for (int i = 0; i < N; ++i) {
-        float v[Q];
+        T v[Q];
 #pragma unroll
-        for (int k = 0; k < Q; ++k) v[k] = src[(i * Q + k) * BH * BW];
-        const float sm = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
-        z += sm;
-        zs[(i * RH + r) * RW + c] = z;
-        hs[(i * RH + r) * RW + c] = P.H[i] + sm;
-      }
-    }
-    // !TAU1 keeps the pre-collision populations of its own cells for C
-    float fo[TAU1 ? 1 : RPT][TAU1 ? 1 : N][Q];
-    if (!TAU1) {
-#pragma unroll
-      for (int rr = 0; rr < RPT; ++rr) {
-        const float* src = stage + (iyb + rr * BY + 2) * BW + (ix + 4);
-#pragma unroll
-        for (int i = 0; i < N; ++i)
-#pragma unroll
-          for (int k = 0; k < Q; ++k) fo[TAU1 ? 0 : rr][TAU1 ? 0 : i][k] = src[(i * Q + k) * BH * BW];
+        for (int k = 0; k < Q; ++k) v[k] = Ln::ld(src + (i * Q + k) * BH * BW, src + (i * Q + k) * BH * BW);
+        z += ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
+        zs[(i * RH + r) * RW + c] = Ln::get(z, 0);
       }
     }
     if (__syncthreads_or(timed_out)) {
@@ -305,103 +309,175 @@ __global__ void __launch_bounds__(256, 2)
       }
       return;
     }
-    // every thread holds what it needs from the stage: refill it with the
-    // next tile, which lands while this tile is finished
-    if (tid == 0) {
-      const int nt = (int)gridDim.x + atomicAdd(sched, 1);
-      next_tile = nt;
-      if (nt < ntiles) issue(nt);
-    }
+    // tau = 1 needs nothing more from the stage: refill it with the next
+    // tile, which lands while this tile is finished
+    if (TAU1 && tid == 0) draw_next();
 
-    // ---- P. pressures on the one-ring region ----------------------------------
-    for (int q = tid; q < PH * PW; q += T::NT) {
-      const int pr = q / PW, pc = q - pr * PW;
-      const int r = pr + 1, c = pc + 1;
-      float h[N], gzx[N], gzy[N], lz[N], p[N];
+    // ---- P. pressures on the one-ring region -------------------------------------
+    // Cell q of the region (row-major, width PW). With packed pairs, rounds of
+    // NT pairs (q, q + NT) cover whole multiples of 2 NT cells and the rest is
+    // done one cell per thread, which keeps the threads evenly loaded.
+    {
+      auto pressure_cells = [&](auto zero, int qa, int qb) {
+        using U = decltype(zero);
+        using LU = Lanes<U>;
+        const int prA = qa / PW, pcA = qa - prA * PW, prB = qb / PW, pcB = qb - prB * PW;
+        U zd[N], gzx[N], gzy[N], lz[N], p[N];
 #pragma unroll
-      for (int i = 0; i < N; ++i) {
-        const float* zc = zs + (i * RH + r) * RW + c;
-        const float zE = zc[1], zW = zc[-1], zN = zc[RW], zS = zc[-RW];
-        const float zNE = zc[RW + 1], zNW = zc[RW - 1], zSE = zc[-RW + 1], zSW = zc[-RW - 1];
-        // (1/cs^2)(w_1 = 1/9, w_2 = 1/36) -> 1/3 and 1/12
-        gzx[i] = (zE - zW) * (1.f / 3.f) + ((zNE - zNW) + (zSE - zSW)) * (1.f / 12.f);
-        gzy[i] = (zN - zS) * (1.f / 3.f) + ((zNE - zSE) + (zNW - zSW)) * (1.f / 12.f);
-        // (2/cs^2) sum_k w_k (z_k - z_0): 2/3 on the edges, 1/6 on the corners
-        lz[i] = ((zE + zW) + (zN + zS)) * (2.f / 3.f) + ((zNE + zNW) + (zSE + zSW)) * (1.f / 6.f) -
-                zc[0] * (10.f / 3.f);
-        h[i] = hs[(i * RH + r) * RW + c];
+        for (int i = 0; i < N; ++i) {
+          const float* a = zs + (i * RH + prA + 1) * RW + pcA + 1;
+          const float* b = zs + (i * RH + prB + 1) * RW + pcB + 1;
+          const U zE = LU::ld(a + 1, b + 1), zW = LU::ld(a - 1, b - 1);
+          const U zN = LU::ld(a + RW, b + RW), zS = LU::ld(a - RW, b - RW);
+          const U zNE = LU::ld(a + RW + 1, b + RW + 1), zNW = LU::ld(a + RW - 1, b + RW - 1);
+          const U zSE = LU::ld(a - RW + 1, b - RW + 1), zSW = LU::ld(a - RW - 1, b - RW - 1);
+          zd[i] = LU::ld(a, b);
+          // (1/cs^2)(w_1 = 1/9, w_2 = 1/36) -> 1/3 and 1/12
+          gzx[i] = fmav(zE - zW, 1.f / 3.f, ((zNE - zNW) + (zSE - zSW)) * (1.f / 12.f));
+          gzy[i] = fmav(zN - zS, 1.f / 3.f, ((zNE - zSE) + (zNW - zSW)) * (1.f / 12.f));
+          // (2/cs^2) sum_k w_k (z_k - z_0): 2/3 on the edges, 1/6 on the corners
+          lz[i] = fmav((zE + zW) + (zN + zS), 2.f / 3.f,
+                       fmav((zNE + zNW) + (zSE + zSW), 1.f / 6.f, zd[i] * (-10.f / 3.f)));
+        }
+        layer_pressures_dev<N, W32, U, NN>(P, zd, gzx, gzy, lz, p);
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+          LU::st(ps + (i * PH + prA) * PW + pcA, ps + (i * PH + prB) * PW + pcB, p[i]);
+      };
+      constexpr int NC = PH * PW;
+      constexpr int NPAIRED = (W == 2) ? (NC / (2 * Tl::NT)) * 2 * Tl::NT : 0;
+      for (int q = tid; q < NPAIRED / 2; q += Tl::NT) {
+        const int base = (q / Tl::NT) * 2 * Tl::NT + q % Tl::NT;
+        pressure_cells(Num<T>::splat(0.f), base, base + Tl::NT);
       }
-      layer_pressures<N, W32>(P, h, gzx, gzy, lz, p);
-#pragma unroll
-      for (int i = 0; i < N; ++i) ps[(i * PH + pr) * PW + pc] = p[i];
+      // the rest one cell per thread, through the same T arithmetic (both
+      // lanes on one cell) so a cell's pressure has the same bits in every tile
+      for (int q = NPAIRED + tid; q < NC; q += Tl::NT) pressure_cells(Num<T>::splat(0.f), q, q);
     }
     __syncthreads();
-    const int tnext = next_tile;  // written by thread 0 before the barrier above
+    // with tau = 1 written by thread 0 before the barrier above
+    int tnext = TAU1 ? next_tile : 0;
 
-    // ---- C. force, collision, streaming -----------------------------------------
+    // ---- C. force, collision, streaming (the thread's rows as one pair) -------
+    {
+      const int iyA = iyb, iyB = iyb + (W - 1) * BY;
+      const int gx = x0 + ix;
+      bool valid[W];
 #pragma unroll
-    for (int rr = 0; rr < RPT; ++rr) {
-      const int iy = iyb + rr * BY;
-      const int gx = x0 + ix, gy = y0 + iy;
-      if (gx >= nx || gy >= ny) continue;
-      float Rx[N], Ry[N];
-      friction<N>(P, hh[rr], jx[rr], jy[rr], Rx, Ry);
-      // destinations of the three column / row offsets and their images
-      int dxs[3], dys[3], xis[3], yis[3];
+      for (int l = 0; l < W; ++l) valid[l] = gx < nx && y0 + iyb + l * BY < ny;
+      if (valid[0]) {  // lane 0 invalid implies lane 1 invalid
+        T hh[N], dd[N], jx[N], jy[N];
+        {
+          T zprev = Num<T>::splat(0.f);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        int dx = gx + c - 1, dy = gy + c - 1;
-        dx += (dx < 0) ? nx : 0;
-        dx -= (dx >= nx) ? nx : 0;
-        dy += (dy < 0) ? ny : 0;
-        dy -= (dy >= ny) ? ny : 0;
-        dxs[c] = dx;
-        dys[c] = dy;
-        xis[c] = image_of(dx, nx);
-        yis[c] = image_of(dy, ny);
-      }
-      const bool images = P.tiny || (xis[0] != kNoImage) || (xis[1] != kNoImage) ||
-                          (xis[2] != kNoImage) || (yis[0] != kNoImage) ||
-                          (yis[1] != kNoImage) || (yis[2] != kNoImage);
-      int koff[Q];
-#pragma unroll
-      for (int k = 0; k < Q; ++k)
-        koff[k] = k * (int)L.plane + (dys[Lattice<2>::cy(k) + 1] + L.gy) * L.pitch +
-                  dxs[Lattice<2>::cx(k) + 1] + L.gx;
-#pragma unroll
-      for (int i = 0; i < N; ++i) {
-        const float* pc = ps + (i * PH + iy + 1) * PW + ix + 1;
-        const float gpx = (pc[1] - pc[-1]) * (1.f / 3.f) +
-                          ((pc[PW + 1] - pc[PW - 1]) + (pc[-PW + 1] - pc[-PW - 1])) * (1.f / 12.f);
-        const float gpy = (pc[PW] - pc[-PW]) * (1.f / 3.f) +
-                          ((pc[PW + 1] - pc[-PW + 1]) + (pc[PW - 1] - pc[-PW - 1])) * (1.f / 12.f);
-        const float h = hh[rr][i];
-        const float Fx = -h * gpx + Rx[i];
-        const float Fy = -h * gpy + Ry[i];
-        bad |= !(h > 0.f) || !isfinite(Fx + Fy);
-        float fs[Q];
-        collide_d2q9<TAU1>(P, h, dd[rr][i], jx[rr][i], jy[rr][i], Fx, Fy,
-                           fo[TAU1 ? 0 : rr][TAU1 ? 0 : i], fs);
-        float* obase = fout + (long)i * lplane;
-        if (!images) {
-#pragma unroll
-          for (int k = 0; k < Q; ++k) obase[koff[k]] = fs[k];
-        } else if (!P.tiny) {
-#pragma unroll
-          for (int k = 0; k < Q; ++k) {
-            const int cxi = Lattice<2>::cx(k) + 1, cyi = Lattice<2>::cy(k) + 1;
-            store_edge(obase + (long)k * L.plane, L, dxs[cxi], dys[cyi], xis[cxi], yis[cyi],
-                       fs[k]);
+          for (int i = 0; i < N; ++i) {
+            const T zi = Ln::ld(zs + (i * RH + iyA + 2) * RW + ix + 2,
+                                zs + (i * RH + iyB + 2) * RW + ix + 2);
+            dd[i] = zi - zprev;
+            zprev = zi;
+            hh[i] = dd[i] + P.H[i];
+            jx[i] = Ln::ld(js + ((0 * N + i) * TY + iyA) * TX + ix, js + ((0 * N + i) * TY + iyB) * TX + ix);
+            jy[i] = Ln::ld(js + ((1 * N + i) * TY + iyA) * TX + ix, js + ((1 * N + i) * TY + iyB) * TX + ix);
           }
-        } else {
+        }
+        T Rx[N], Ry[N];
+        friction<N>(P, hh, jx, jy, Rx, Ry);
+        // A tile at least three cells from every edge streams without
+        // wrap-around or ghost images: all nine destinations are fixed,
+        // warp-uniform offsets from one base per cell.
+        const bool inner = !P.tiny && x0 >= 3 && x0 + TX + 3 <= nx && y0 >= 3 && y0 + TY + 3 <= ny;
+        float* cbase[W];
 #pragma unroll
-          for (int k = 0; k < Q; ++k) {
-            const int cxi = Lattice<2>::cx(k) + 1, cyi = Lattice<2>::cy(k) + 1;
-            store_images(obase + (long)k * L.plane, L, dxs[cxi], dys[cyi],
-                         ghost_mask(P.gsrcx, dxs[cxi]), ghost_mask(P.gsrcy, dys[cyi]), fs[k]);
+        for (int l = 0; l < W; ++l)
+          cbase[l] = fout + (long)(y0 + iyb + l * BY + L.gy) * L.pitch + (gx + L.gx);
+        // per lane: destinations of the three column / row offsets, images
+        int koff[W][Q], dxs[W][3], dys[W][3], xis[W][3], yis[W][3];
+        bool images[W];
+#pragma unroll
+        for (int l = 0; l < W && !inner; ++l) {
+          const int gy = y0 + iyb + l * BY;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            int dx = gx + c - 1, dy = gy + c - 1;
+            dx += (dx < 0) ? nx : 0;
+            dx -= (dx >= nx) ? nx : 0;
+            dy += (dy < 0) ? ny : 0;
+            dy -= (dy >= ny) ? ny : 0;
+            dxs[l][c] = dx;
+            dys[l][c] = dy;
+            xis[l][c] = image_of(dx, nx);
+            yis[l][c] = image_of(dy, ny);
+          }
+          // lattices with a side below 4 cells refresh their ghosts in a
+          // separate pass; the others write the images here
+          images[l] = !P.tiny && ((xis[l][0] != kNoImage) || (xis[l][1] != kNoImage) ||
+                                  (xis[l][2] != kNoImage) || (yis[l][0] != kNoImage) ||
+                                  (yis[l][1] != kNoImage) || (yis[l][2] != kNoImage));
+#pragma unroll
+          for (int k = 0; k < Q; ++k)
+            koff[l][k] = k * (int)L.plane + (dys[l][Lattice<2>::cy(k) + 1] + L.gy) * L.pitch +
+                         dxs[l][Lattice<2>::cx(k) + 1] + L.gx;
+        }
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          const float* a = ps + (i * PH + iyA + 1) * PW + ix + 1;
+          const float* b = ps + (i * PH + iyB + 1) * PW + ix + 1;
+          const T pE = Ln::ld(a + 1, b + 1), pW = Ln::ld(a - 1, b - 1);
+          const T pN = Ln::ld(a + PW, b + PW), pS = Ln::ld(a - PW, b - PW);
+          const T pNE = Ln::ld(a + PW + 1, b + PW + 1), pNW = Ln::ld(a + PW - 1, b + PW - 1);
+          const T pSE = Ln::ld(a - PW + 1, b - PW + 1), pSW = Ln::ld(a - PW - 1, b - PW - 1);
+          const T gpx = fmav(pE - pW, 1.f / 3.f, ((pNE - pNW) + (pSE - pSW)) * (1.f / 12.f));
+          const T gpy = fmav(pN - pS, 1.f / 3.f, ((pNE - pSE) + (pNW - pSW)) * (1.f / 12.f));
+          const T h = hh[i];
+          const T Fx = fmav(-h, gpx, Rx[i]);
+          const T Fy = fmav(-h, gpy, Ry[i]);
+#pragma unroll
+          for (int l = 0; l < W; ++l)
+            if (valid[l])
+              bad |= !(Ln::get(h, l) > 0.f) || !isfinite(Ln::get(Fx, l) + Ln::get(Fy, l));
+          T fo[Q];
+          if constexpr (!TAU1) {
+            const float* sA = stage + (iyA + 2) * BW + (ix + 4);
+            const float* sB = stage + (iyB + 2) * BW + (ix + 4);
+#pragma unroll
+            for (int k = 0; k < Q; ++k) fo[k] = Ln::ld(sA + (i * Q + k) * BH * BW, sB + (i * Q + k) * BH * BW);
+          }
+          T fs[Q];
+          collide_d2q9<TAU1>(P, h, dd[i], jx[i], jy[i], Fx, Fy, fo, fs);
+          if (inner) {
+#pragma unroll
+            for (int l = 0; l < W; ++l) {
+#pragma unroll
+              for (int k = 0; k < Q; ++k)
+                cbase[l][(long)i * lplane + (long)k * L.plane +
+                         Lattice<2>::cy(k) * L.pitch + Lattice<2>::cx(k)] = Ln::get(fs[k], l);
+            }
+            continue;
+          }
+          float* obase = fout + (long)i * lplane;
+#pragma unroll
+          for (int l = 0; l < W; ++l) {
+            if (!valid[l]) continue;
+            if (!images[l]) {
+#pragma unroll
+              for (int k = 0; k < Q; ++k) obase[koff[l][k]] = Ln::get(fs[k], l);
+            } else {
+#pragma unroll
+              for (int k = 0; k < Q; ++k) {
+                const int cxi = Lattice<2>::cx(k) + 1, cyi = Lattice<2>::cy(k) + 1;
+                store_edge(obase + (long)k * L.plane, L, dxs[l][cxi], dys[l][cyi], xis[l][cxi],
+                           yis[l][cyi], Ln::get(fs[k], l));
+              }
+            }
           }
         }
       }
+    }
+    if (!TAU1) {
+      __syncthreads();  // every thread has read its pre-collision populations
+      if (tid == 0) draw_next();
+      __syncthreads();
+      tnext = next_tile;
     }
     t = tnext;
   }
@@ -422,8 +498,7 @@ __global__ void __launch_bounds__(TX)
                      int* __restrict__ status) {
   constexpr int Q = 3;
   constexpr int RW = TX + 4, PW = TX + 2;
-  __shared__ float zs[N][RW];
-  __shared__ float hs[N][RW];
+  __shared__ float zs[N][RW];  // interface-height deviations, see D2Q9
   __shared__ float ps[N][PW];
   const Layout& L = P.L;
   const int nx = P.nx;
@@ -442,7 +517,6 @@ __global__ void __launch_bounds__(TX)
       hh[i] = P.H[i] + s;
       jx[i] = f1 - f2;
       z += s;
-      hs[i][tx + 2] = hh[i];
       zs[i][tx + 2] = z;
     }
   }
@@ -452,27 +526,25 @@ __global__ void __launch_bounds__(TX)
     float z = 0.f;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      const float s = __ldg(fin + L.at(i * Q + 0, x, 0)) +
-                      (__ldg(fin + L.at(i * Q + 1, x, 0)) + __ldg(fin + L.at(i * Q + 2, x, 0)));
-      z += s;
-      hs[i][rc] = P.H[i] + s;
+      z += __ldg(fin + L.at(i * Q + 0, x, 0)) +
+           (__ldg(fin + L.at(i * Q + 1, x, 0)) + __ldg(fin + L.at(i * Q + 2, x, 0)));
       zs[i][rc] = z;
     }
   }
   __syncthreads();
   for (int pc = tx; pc < PW; pc += TX) {
     const int rc = pc + 1;
-    float h[N], gxz[N], gyz[N], lz[N], p[N];
+    float zd[N], gxz[N], gyz[N], lz[N], p[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) {
       const float c = zs[i][rc];
       const float e = zs[i][rc + 1] - c, wv = zs[i][rc - 1] - c;
+      zd[i] = c;
       gxz[i] = 0.5f * (e - wv);  // (1/cs^2) w_1 = 1/2
       gyz[i] = 0.f;
       lz[i] = e + wv;            // (2/cs^2) w_1 = 1
-      h[i] = hs[i][rc];
     }
-    layer_pressures<N, W32>(P, h, gxz, gyz, lz, p);
+    layer_pressures_dev<N, W32>(P, zd, gxz, gyz, lz, p);
 #pragma unroll
     for (int i = 0; i < N; ++i) ps[i][pc] = p[i];
   }
@@ -490,7 +562,7 @@ __global__ void __launch_bounds__(TX)
     dx += (dx < 0) ? nx : 0;
     dx -= (dx >= nx) ? nx : 0;
     dxs[c] = dx;
-    xis[c] = image_of(dx, nx);
+    xis[c] = P.tiny ? kNoImage : image_of(dx, nx);  // tiny lattices refresh ghosts apart
   }
   bool bad = false;
 #pragma unroll
@@ -510,11 +582,7 @@ __global__ void __launch_bounds__(TX)
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
       const int cxi = Lattice<1>::cx(k) + 1;
-      float* base = fout + (long)(i * Q + k) * L.plane;
-      if (!P.tiny)
-        store_edge(base, L, dxs[cxi], 0, xis[cxi], kNoImage, fs[k]);
-      else
-        store_images(base, L, dxs[cxi], 0, ghost_mask(P.gsrcx, dxs[cxi]), 0u, fs[k]);
+      store_edge(fout + (long)(i * Q + k) * L.plane, L, dxs[cxi], 0, xis[cxi], kNoImage, fs[k]);
     }
   }
   if (bad) atomicOr(status, kStatusNonfinite);
@@ -525,10 +593,10 @@ __global__ void __launch_bounds__(TX)
 // ---------------------------------------------------------------------------
 constexpr int kD1TX = 128;
 
-template <int N, bool TAU1, bool W32>
+template <int N, int MODE>
 static cudaError_t launch_d2(const StepLaunch& a, cudaStream_t st) {
   using T = D2Tile<N>;
-  auto kern = step_d2q9_tma<N, TAU1, W32>;
+  auto kern = step_d2q9_tma<N, MODE>;
   // raise the dynamic shared-memory limit and size the persistent grid once
   // per device and instantiation
   static unsigned long long configured = 0;
@@ -553,31 +621,39 @@ static cudaError_t launch_d2(const StepLaunch& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <int N, bool TAU1, bool W32>
+template <int N>
 static cudaError_t launch_n(const StepLaunch& a, cudaStream_t st) {
-  if (a.lattice == 2) return launch_d2<N, TAU1, W32>(a, st);
+  const bool tau1 = (a.P.omega == 1.f);
+  const bool w32 = (a.P.nw == 3 && a.P.mw == 2);
+  bool nn = true;  // spreading coefficients only between neighbouring interfaces
+  for (int l = 0; l < N; ++l)
+    for (int k = 2; k <= N - l; ++k) nn = nn && (a.P.S[l][k - 1] == 0.f);
+  if (a.lattice == 2) {
+    if (!tau1) return launch_d2<N, kGeneral>(a, st);
+    if (w32 && nn) return launch_d2<N, kFast>(a, st);
+    return launch_d2<N, kTau1>(a, st);
+  }
   dim3 grid((a.P.nx + kD1TX - 1) / kD1TX);
-  step_d1q3_kernel<N, kD1TX, TAU1, W32><<<grid, kD1TX, 0, st>>>(a.fin, a.fout, a.P, a.status);
+  if (tau1) {
+    if (w32)
+      step_d1q3_kernel<N, kD1TX, true, true><<<grid, kD1TX, 0, st>>>(a.fin, a.fout, a.P, a.status);
+    else
+      step_d1q3_kernel<N, kD1TX, true, false><<<grid, kD1TX, 0, st>>>(a.fin, a.fout, a.P, a.status);
+  } else {
+    step_d1q3_kernel<N, kD1TX, false, false><<<grid, kD1TX, 0, st>>>(a.fin, a.fout, a.P, a.status);
+  }
   return cudaGetLastError();
 }
 
-template <bool TAU1, bool W32>
-static cudaError_t launch_tau(const StepLaunch& a, cudaStream_t st) {
+cudaError_t launch_step(const StepLaunch& a, cudaStream_t st) {
   switch (a.P.n) {
-    case 1: return launch_n<1, TAU1, W32>(a, st);
-    case 2: return launch_n<2, TAU1, W32>(a, st);
-    case 3: return launch_n<3, TAU1, W32>(a, st);
-    case 4: return launch_n<4, TAU1, W32>(a, st);
-    case 5: return launch_n<5, TAU1, W32>(a, st);
+    case 1: return launch_n<1>(a, st);
+    case 2: return launch_n<2>(a, st);
+    case 3: return launch_n<3>(a, st);
+    case 4: return launch_n<4>(a, st);
+    case 5: return launch_n<5>(a, st);
     default: return cudaErrorInvalidValue;
   }
-}
-
-cudaError_t launch_step(const StepLaunch& a, cudaStream_t st) {
-  const bool w32 = (a.P.nw == 3 && a.P.mw == 2);
-  const bool tau1 = (a.P.omega == 1.f);
-  if (tau1) return w32 ? launch_tau<true, true>(a, st) : launch_tau<true, false>(a, st);
-  return w32 ? launch_tau<false, true>(a, st) : launch_tau<false, false>(a, st);
 }
 
 int step_tile_cols(int lattice) { return lattice == 2 ? 32 : kD1TX; }
