@@ -305,7 +305,7 @@ def run_own(args):
             "config": config_dict(),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "step_d2q9_kernel<3,8,2,true>",
+                         "kernel": "step_d2q9_tma<3,kFast>",
                          "bytes_per_launch_algorithmic": bytes_alg, "peak_source": peak_src},
             "e2e": {"value": ws * lsu_step * k_e2e / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": int(h_host.numel() * 4),
