@@ -132,7 +132,9 @@ int mlswlbm_step(mlsw_handle* h, long nsteps);
 
 /* Heights h_i = sum_k f_ki into out (host, n*nx*ny floats). Synchronises.
  * Returns MLSW_ERR_NONFINITE if any step since create or the last status
- * query flagged h <= 0 or a non-finite value (out is still written). */
+ * query flagged h <= 0 or a non-finite value (out is still written).
+ * Page-locked memory (cudaHostAlloc, cudaHostRegister) is written by the
+ * read-out kernel directly; other memory through a device buffer. */
 int mlswlbm_get_heights(mlsw_handle* h, float* out);
 
 /* Same into device memory dev_out (n*nx*ny floats, caller-owned, on the
@@ -144,7 +146,9 @@ int mlswlbm_get_heights_device(mlsw_handle* h, float* dev_out);
  * as MLSW_ERR_NONFINITE by the next status query (mlswlbm_status,
  * mlswlbm_get_heights, mlswlbm_get_diagnostics). The shift H_i of create is
  * kept. Asynchronous on the handle's stream; h_in must stay valid until the
- * stream reaches the copy (pageable memory is copied before return). */
+ * stream reaches the copy (pageable memory is copied before return).
+ * Page-locked memory is read by the initialisation kernel directly, so it
+ * must stay unchanged until that kernel has run. */
 int mlswlbm_set_heights(mlsw_handle* h, const float* h_in);
 
 /* True population state (host, n*Q*nx*ny floats, layout above): copy out

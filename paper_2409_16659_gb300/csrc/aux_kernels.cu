@@ -3,6 +3,7 @@
 // evaluation. All population arrays use the padded Layout of physics.cuh
 // (a dense caller array is the Layout with no ghosts).
 #include <cfloat>
+#include <cstdint>
 
 #include "kernels.h"
 #include "physics.cuh"
@@ -17,34 +18,145 @@ static int grid_for(long work, int threads) {
 }
 
 // ---------------------------------------------------------------------------
-// f = f_eq(h, U = 0) (Eq. equilibrium_distribution at rest): f_0 = h, else 0
+// Row-parallel kernels: blockIdx.x covers the x range of a row in chunks of
+// blockDim.x, blockIdx.y runs (grid-stride) over the rows. Index arithmetic
+// stays in 32 bits per row; only the final offsets are 64-bit.
 // ---------------------------------------------------------------------------
-__global__ void init_kernel(int Q, int n, Layout L, const float* __restrict__ h,
-                            float* __restrict__ f, KShift sh, int* __restrict__ status) {
-  const long ncell = (long)L.nx * L.ny;
-  const long total = (long)n * Q * ncell;
+constexpr int kRowThreads = 256;
+
+// About 4096 blocks in all, each looping over many rows: a block per row
+// would spend more time being scheduled than storing its one row segment.
+static dim3 row_grid(int width, long nrows) {
+  const long gx = (width + kRowThreads - 1) / kRowThreads;
+  long gy = 4096 / gx;
+  if (gy > nrows) gy = nrows;
+  if (gy > 65535) gy = 65535;
+  if (gy < 1) gy = 1;
+  return dim3((unsigned)gx, (unsigned)gy, 1);
+}
+
+__device__ __forceinline__ int wrap_any(int v, int n) {
+  v %= n;
+  return v < 0 ? v + n : v;
+}
+
+// Lanes of V consecutive x (V = 4: one 16-byte access).
+template <int V>
+struct Row;
+template <>
+struct Row<1> {
+  using T = float;
+  static __device__ __forceinline__ T load(const float* p) { return *p; }
+  static __device__ __forceinline__ void store(float* p, T v) { *p = v; }
+  static __device__ __forceinline__ T sub(T a, float b) { return a - b; }
+  static __device__ __forceinline__ T add(T a, T b) { return a + b; }
+  static __device__ __forceinline__ T splat(float b) { return b; }
+  static __device__ __forceinline__ bool ok(T v) { return v > 0.f && isfinite(v); }
+};
+template <>
+struct Row<4> {
+  using T = float4;
+  static __device__ __forceinline__ T load(const float* p) {
+    return *reinterpret_cast<const float4*>(p);
+  }
+  static __device__ __forceinline__ void store(float* p, T v) {
+    *reinterpret_cast<float4*>(p) = v;
+  }
+  static __device__ __forceinline__ T sub(T a, float b) {
+    return make_float4(a.x - b, a.y - b, a.z - b, a.w - b);
+  }
+  static __device__ __forceinline__ T add(T a, T b) {
+    return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+  }
+  static __device__ __forceinline__ T splat(float b) { return make_float4(b, b, b, b); }
+  static __device__ __forceinline__ bool ok(T v) {
+    return Row<1>::ok(v.x) && Row<1>::ok(v.y) && Row<1>::ok(v.z) && Row<1>::ok(v.w);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// f = f_eq(h, U = 0) (Eq. equilibrium_distribution at rest): f_0 = h, else 0.
+// One thread owns V cells of a padded row of one layer, reads their heights
+// once and writes all Q planes. The x range [-4, nx + 4) covers the ghost
+// ring and the two alignment columns on each side, and y runs over
+// [-2, ny + 2) when ghosts_y: every ghost takes its periodic image, so no
+// separate ghost pass is needed. R rows are in flight per thread, which
+// matters when h is page-locked host memory read across the host link.
+// ---------------------------------------------------------------------------
+template <int Q, int V>
+__global__ void __launch_bounds__(kRowThreads)
+    init_kernel(int n, Layout L, int ghosts_y, const float* __restrict__ h,
+                float* __restrict__ f, KShift sh, int* __restrict__ status) {
+  using Rw = Row<V>;
+  using T = typename Rw::T;
+  constexpr int R = 4;
+  const int nx = L.nx, ny = L.ny;
+  const int groups = (nx + 8) / V;
+  const int yrows = ghosts_y ? ny + 4 : 1;
+  const int y0 = ghosts_y ? 2 : 0;
+  const long nrows = (long)n * yrows;
+  const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= groups) return;
+  const int x = gi * V - 4;
+  // V = 4 needs nx % 4 == 0, so a group of x maps onto one group of sx
+  const int sx = (x >= 0 && x < nx) ? x : wrap_any(x, nx);
   bool bad = false;
-  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total;
-       t += (long)gridDim.x * blockDim.x) {
-    const long cell = t % ncell;
-    const int p = (int)(t / ncell);
-    const int k = p % Q, i = p / Q;
-    const int x = (int)(cell % L.nx), y = (int)(cell / L.nx);
-    float v = 0.f;
-    if (k == 0) {
-      const float hv = h[(long)i * ncell + cell];
-      bad |= !(hv > 0.f) || !isfinite(hv);
-      v = hv - sh.H[i];  // stored rest population is shifted by H_i
+  for (long r0 = blockIdx.y; r0 < nrows; r0 += (long)R * gridDim.y) {
+    T hv[R];
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+      const long r = r0 + (long)u * gridDim.y;
+      if (r < nrows) {
+        const int i = (int)(r / yrows);
+        const int y = (int)(r - (long)i * yrows) - y0;
+        const int sy = ghosts_y ? ((y >= 0 && y < ny) ? y : wrap_any(y, ny)) : 0;
+        hv[u] = Rw::load(h + ((long)i * ny + sy) * nx + sx);
+      }
     }
-    f[L.at(p, x, y)] = v;
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+      const long r = r0 + (long)u * gridDim.y;
+      if (r < nrows) {
+        const int i = (int)(r / yrows);
+        const int y = (int)(r - (long)i * yrows) - y0;
+        bad |= !Rw::ok(hv[u]);
+        float* dst = f + L.at(i * Q, x, y);
+        Rw::store(dst, Rw::sub(hv[u], sh.H[i]));  // rest population, shifted by H_i
+#pragma unroll
+        for (int k = 1; k < Q; ++k) Rw::store(dst + (long)k * L.plane, Rw::splat(0.f));
+      }
+    }
   }
   if (bad) atomicOr(status, kStatusNonfinite);
 }
 
-cudaError_t launch_init(int Q, int n, const Layout& L, const float* h, float* f, const KShift& sh,
-                        int* status, cudaStream_t st) {
-  const long total = (long)n * Q * L.nx * L.ny;
-  init_kernel<<<grid_for(total, 256), 256, 0, st>>>(Q, n, L, h, f, sh, status);
+template <int Q>
+static void init_q(const dim3& g, int V, int n, const Layout& L, int gy, const float* h,
+                   float* f, const KShift& sh, int* status, cudaStream_t st) {
+  if (V == 4)
+    init_kernel<Q, 4><<<g, kRowThreads, 0, st>>>(n, L, gy, h, f, sh, status);
+  else
+    init_kernel<Q, 1><<<g, kRowThreads, 0, st>>>(n, L, gy, h, f, sh, status);
+}
+
+cudaError_t launch_init(int Q, int n, const Layout& L, bool ghosts_y, const float* h, float* f,
+                        const KShift& sh, int* status, cudaStream_t st) {
+  // the written x range [-4, nx + 4) and y range [-2, ny + 2) must lie
+  // inside the padding
+  if (L.gx != 4 || L.pitch < L.nx + 8 || (ghosts_y && (L.gy != 2 || L.rows < L.ny + 4)))
+    return cudaErrorInvalidValue;
+  const bool vec = L.nx % 4 == 0 && L.nx >= 4 && (reinterpret_cast<uintptr_t>(h) & 15) == 0 &&
+                   (reinterpret_cast<uintptr_t>(f) & 15) == 0 && L.pitch % 4 == 0 &&
+                   L.gx == 4 && L.plane % 4 == 0;
+  const int V = vec ? 4 : 1;
+  const long nrows = (long)n * (ghosts_y ? L.ny + 4 : 1);
+  const dim3 g = row_grid((L.nx + 8) / V, nrows);
+  if (Q == 9)
+    init_q<9>(g, V, n, L, ghosts_y ? 1 : 0, h, f, sh, status, st);
+  else if (Q == 3)
+    init_q<3>(g, V, n, L, ghosts_y ? 1 : 0, h, f, sh, status, st);
+  else
+    return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
@@ -53,11 +165,6 @@ cudaError_t launch_init(int Q, int n, const Layout& L, const float* h, float* f,
 // columns x in {-2, -1, nx, nx + 1} over y in [0, ny) (x only: the columns
 // over y = 0)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int wrap_any(int v, int n) {
-  v %= n;
-  return v < 0 ? v + n : v;
-}
-
 __global__ void fill_ghosts_kernel(int nplanes, Layout L, int ghosts_y, float* __restrict__ f) {
   const int nx = L.nx, ny = L.ny;
   const long rows_part = ghosts_y ? 4L * (nx + 4) : 0;  // four ghost rows
@@ -93,63 +200,91 @@ cudaError_t launch_fill_ghosts(int nplanes, const Layout& L, bool ghosts_y, floa
 }
 
 // ---------------------------------------------------------------------------
-// read-out and representation shifts (real cells only)
+// read-out and representation shifts (real cells only; one row = one layer
+// row y of the lattice)
 // ---------------------------------------------------------------------------
-__global__ void heights_kernel(int Q, int n, Layout L, const float* __restrict__ f, KShift sh,
-                               float* __restrict__ h) {
-  const long ncell = (long)L.nx * L.ny;
-  const long total = (long)n * ncell;
-  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total;
-       t += (long)gridDim.x * blockDim.x) {
-    const long cell = t % ncell;
-    const int i = (int)(t / ncell);
-    const int x = (int)(cell % L.nx), y = (int)(cell / L.nx);
-    float s = 0.f;
-    for (int k = 0; k < Q; ++k) s += f[L.at(i * Q + k, x, y)];
-    h[t] = sh.H[i] + s;
+template <int Q, int V>
+__global__ void __launch_bounds__(kRowThreads)
+    heights_kernel(int n, Layout L, const float* __restrict__ f, KShift sh,
+                   float* __restrict__ h) {
+  using Rw = Row<V>;
+  using T = typename Rw::T;
+  const int nx = L.nx, ny = L.ny;
+  const int x = (blockIdx.x * blockDim.x + threadIdx.x) * V;
+  if (x >= nx) return;
+  for (long r = blockIdx.y; r < (long)n * ny; r += gridDim.y) {
+    const int i = (int)(r / ny), y = (int)(r - (long)i * ny);
+    const float* src = f + L.at(i * Q, x, y);
+    T v[Q];
+#pragma unroll
+    for (int k = 0; k < Q; ++k) v[k] = Rw::load(src + (long)k * L.plane);
+    T s = Rw::splat(sh.H[i]);
+    T d = Rw::splat(0.f);
+#pragma unroll
+    for (int k = 0; k < Q; ++k) d = Rw::add(d, v[k]);
+    Rw::store(h + r * nx + x, Rw::add(s, d));
   }
+}
+
+template <int Q>
+static void heights_q(const dim3& g, int V, int n, const Layout& L, const float* f,
+                      const KShift& sh, float* h, cudaStream_t st) {
+  if (V == 4)
+    heights_kernel<Q, 4><<<g, kRowThreads, 0, st>>>(n, L, f, sh, h);
+  else
+    heights_kernel<Q, 1><<<g, kRowThreads, 0, st>>>(n, L, f, sh, h);
 }
 
 cudaError_t launch_heights(int Q, int n, const Layout& L, const float* f, const KShift& sh,
                            float* h, cudaStream_t st) {
-  heights_kernel<<<grid_for((long)n * L.nx * L.ny, 256), 256, 0, st>>>(Q, n, L, f, sh, h);
+  const bool vec = L.nx % 4 == 0 && (reinterpret_cast<uintptr_t>(h) & 15) == 0 &&
+                   (reinterpret_cast<uintptr_t>(f) & 15) == 0 && L.pitch % 4 == 0 &&
+                   L.gx % 4 == 0 && L.plane % 4 == 0;
+  const int V = vec ? 4 : 1;
+  const dim3 g = row_grid(L.nx / V, (long)n * L.ny);
+  if (Q == 9)
+    heights_q<9>(g, V, n, L, f, sh, h, st);
+  else if (Q == 3)
+    heights_q<3>(g, V, n, L, f, sh, h, st);
+  else
+    return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
-__global__ void shift_kernel(int Q, int n, Layout L, float* __restrict__ f, KShift sh,
-                             float sign) {
-  const long ncell = (long)L.nx * L.ny;
-  const long total = (long)n * ncell;
-  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total;
-       t += (long)gridDim.x * blockDim.x) {
-    const long cell = t % ncell;
-    const int i = (int)(t / ncell);
-    float* p = f + L.at(i * Q, (int)(cell % L.nx), (int)(cell / L.nx));
+__global__ void __launch_bounds__(kRowThreads)
+    shift_kernel(int Q, int n, Layout L, float* __restrict__ f, KShift sh, float sign) {
+  const int nx = L.nx, ny = L.ny;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= nx) return;
+  for (long r = blockIdx.y; r < (long)n * ny; r += gridDim.y) {
+    const int i = (int)(r / ny), y = (int)(r - (long)i * ny);
+    float* p = f + L.at(i * Q, x, y);
     *p = *p + sign * sh.H[i];
   }
 }
 
 cudaError_t launch_shift(int Q, int n, const Layout& L, float* f, const KShift& sh, float sign,
                          cudaStream_t st) {
-  shift_kernel<<<grid_for((long)n * L.nx * L.ny, 256), 256, 0, st>>>(Q, n, L, f, sh, sign);
+  shift_kernel<<<row_grid(L.nx, (long)n * L.ny), kRowThreads, 0, st>>>(Q, n, L, f, sh, sign);
   return cudaGetLastError();
 }
 
-__global__ void rest_planes_kernel(int Q, int n, Layout L, const float* __restrict__ f, KShift sh,
-                                   float* __restrict__ out) {
-  const long ncell = (long)L.nx * L.ny;
-  const long total = (long)n * ncell;
-  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total;
-       t += (long)gridDim.x * blockDim.x) {
-    const long cell = t % ncell;
-    const int i = (int)(t / ncell);
-    out[t] = sh.H[i] + f[L.at(i * Q, (int)(cell % L.nx), (int)(cell / L.nx))];
+__global__ void __launch_bounds__(kRowThreads)
+    rest_planes_kernel(int Q, int n, Layout L, const float* __restrict__ f, KShift sh,
+                       float* __restrict__ out) {
+  const int nx = L.nx, ny = L.ny;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= nx) return;
+  for (long r = blockIdx.y; r < (long)n * ny; r += gridDim.y) {
+    const int i = (int)(r / ny), y = (int)(r - (long)i * ny);
+    out[r * nx + x] = sh.H[i] + f[L.at(i * Q, x, y)];
   }
 }
 
 cudaError_t launch_rest_planes(int Q, int n, const Layout& L, const float* f, const KShift& sh,
                                float* out, cudaStream_t st) {
-  rest_planes_kernel<<<grid_for((long)n * L.nx * L.ny, 256), 256, 0, st>>>(Q, n, L, f, sh, out);
+  rest_planes_kernel<<<row_grid(L.nx, (long)n * L.ny), kRowThreads, 0, st>>>(Q, n, L, f, sh,
+                                                                             out);
   return cudaGetLastError();
 }
 

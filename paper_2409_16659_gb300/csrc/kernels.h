@@ -36,11 +36,12 @@ cudaError_t launch_step(const StepLaunch& a, cudaStream_t st);
 int step_tile_cols(int lattice);
 int step_tile_rows(int n, int lattice);
 
-// f = f_eq(h, U = 0) on the real cells: rest population h - H_i, moving
-// populations 0; h dense [n][ny][nx]. status |= kStatusNonfinite where
-// h <= 0 or h is not finite. Ghost cells are left to launch_fill_ghosts.
-cudaError_t launch_init(int Q, int n, const Layout& L, const float* h, float* f, const KShift& sh,
-                        int* status, cudaStream_t st);
+// f = f_eq(h, U = 0) on the real cells and their ghost images (x only
+// when ghosts_y is false): rest population h - H_i, moving populations 0;
+// h dense [n][ny][nx]. status |= kStatusNonfinite where h <= 0 or h is not
+// finite.
+cudaError_t launch_init(int Q, int n, const Layout& L, bool ghosts_y, const float* h, float* f,
+                        const KShift& sh, int* status, cudaStream_t st);
 
 // Periodic images: every ghost cell within two cells of the real domain
 // (x only when ghosts_y is false) copies its real cell, for all nplanes

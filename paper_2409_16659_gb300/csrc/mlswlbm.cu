@@ -249,6 +249,19 @@ void set_shift(mlsw_handle* h, const float* H) {
     }
 }
 
+// The address at which kernels on the current device can read or write a
+// page-locked host buffer, or nullptr when p is pageable or device memory.
+// Kernels then move the heights across the host link themselves, fused
+// with the initialisation or the read-out, instead of a separate copy.
+const void* mapped_host_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 }  // namespace
 
 extern "C" {
@@ -423,13 +436,17 @@ int mlswlbm_create(const mlsw_params* p, const float* h_init, void* stream, mlsw
 
 int mlswlbm_set_heights(mlsw_handle* h, const float* h_in) {
   if (!h || !h_in) return MLSW_ERR_ARG;
-  const size_t bytes = (size_t)h->p.n_layers * h->ncell * sizeof(float);
-  CU(cudaMemcpyAsync(h->hbuf, h_in, bytes, cudaMemcpyHostToDevice, h->stream));
-  CU(mlsw::launch_init(h->Q, h->p.n_layers, h->kp.L, h->hbuf, h->f[h->cur], h->sh, h->status,
-                       h->stream));
-  CU(mlsw::launch_fill_ghosts(h->p.n_layers * h->Q, h->kp.L, h->p.lattice == MLSW_D2Q9,
-                              h->f[h->cur], h->stream));
-  h->launches += 2;
+  // page-locked heights are read by the init kernel in place; others are
+  // copied to the device first
+  const float* src = static_cast<const float*>(mapped_host_ptr(h_in));
+  if (!src) {
+    const size_t bytes = (size_t)h->p.n_layers * h->ncell * sizeof(float);
+    CU(cudaMemcpyAsync(h->hbuf, h_in, bytes, cudaMemcpyHostToDevice, h->stream));
+    src = h->hbuf;
+  }
+  CU(mlsw::launch_init(h->Q, h->p.n_layers, h->kp.L, h->p.lattice == MLSW_D2Q9, src,
+                       h->f[h->cur], h->sh, h->status, h->stream));
+  h->launches += 1;
   return MLSW_OK;
 }
 
@@ -481,10 +498,14 @@ int mlswlbm_get_heights_device(mlsw_handle* h, float* dev_out) {
 
 int mlswlbm_get_heights(mlsw_handle* h, float* out) {
   if (!h || !out) return MLSW_ERR_ARG;
-  int rc = mlswlbm_get_heights_device(h, h->hbuf);
+  // page-locked output is written by the read-out kernel in place
+  float* mapped = static_cast<float*>(const_cast<void*>(mapped_host_ptr(out)));
+  int rc = mlswlbm_get_heights_device(h, mapped ? mapped : h->hbuf);
   if (rc != MLSW_OK) return rc;
-  const size_t bytes = (size_t)h->p.n_layers * h->ncell * sizeof(float);
-  CU(cudaMemcpyAsync(out, h->hbuf, bytes, cudaMemcpyDeviceToHost, h->stream));
+  if (!mapped) {
+    const size_t bytes = (size_t)h->p.n_layers * h->ncell * sizeof(float);
+    CU(cudaMemcpyAsync(out, h->hbuf, bytes, cudaMemcpyDeviceToHost, h->stream));
+  }
   return mlswlbm_status(h);
 }
 

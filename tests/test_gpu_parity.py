@@ -240,4 +240,32 @@ def test_torch_stream_binding_and_launch_count():
         a.step(40)
         b.step(40)
         assert np.array_equal(a.get_heights(), b.get_heights())
-        assert a.launch_count() == 2 + 40 + 1  # init + ghost images, steps, read-out
+        assert a.launch_count() == 1 + 40 + 1  # init (with ghost images), steps, read-out
+
+
+def test_pinned_host_heights_match_pageable():
+    """Page-locked heights go through the kernels in place (no staging
+    copy); the results equal those of pageable buffers bit for bit."""
+    import torch
+    p = workloads.film3_d2q9_params(72, 40)
+    h0 = workloads.film3_d2q9_heights(72, 40).astype(np.float32)
+    pin_in = torch.from_numpy(h0.copy()).pin_memory()
+    pin_out = torch.zeros(h0.shape, dtype=torch.float32).pin_memory()
+    with B.Solver(p, h0) as a, B.Solver(p, h0) as b:
+        a.step(7)
+        b.step(7)
+        ref = a.get_heights()
+        b.get_heights(pin_out.numpy())
+        assert np.array_equal(pin_out.numpy(), ref)
+        a.set_heights(h0)
+        b.set_heights(pin_in.numpy())
+        a.step(5)
+        b.step(5)
+        assert np.array_equal(a.get_state(), b.get_state())
+        assert np.array_equal(a.get_heights(), b.get_heights(pin_out.numpy()))
+        bad = h0.copy()
+        bad[1, 3, 4] = -1.0
+        pin_bad = torch.from_numpy(bad).pin_memory()
+        with pytest.raises(B.MlswError):
+            b.set_heights(pin_bad.numpy())
+            b.get_heights(pin_out.numpy())
