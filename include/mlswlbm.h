@@ -52,6 +52,10 @@ extern "C" {
 
 /* flags */
 #define MLSW_FLAG_SKIP_STABILITY_CHECK 1
+/* D1Q3 lattices that fit one CTA's shared memory normally run all the
+ * steps of one mlswlbm_step call in a single persistent launch; this flag
+ * keeps them on one launch per step (same results, bit for bit). */
+#define MLSW_FLAG_NO_PERSISTENT 2
 
 /* return codes */
 #define MLSW_OK 0
@@ -125,9 +129,12 @@ int mlswlbm_check_params(const mlsw_params* p);
 int mlswlbm_create(const mlsw_params* p, const float* h_init, void* stream,
                    mlsw_handle** out);
 
-/* Enqueues nsteps >= 0 time steps (one fused kernel launch per step) on the
- * handle's stream; asynchronous. MLSW_ERR_ARG for a NULL handle or
- * nsteps < 0; MLSW_ERR_CUDA if a launch fails. */
+/* Enqueues nsteps >= 0 time steps on the handle's stream; asynchronous.
+ * One fused kernel launch per step, except for D1Q3 lattices small enough
+ * for one CTA (8 n nx floats of shared memory), which run up to 16384 steps
+ * per persistent launch with the lattice held on chip (see
+ * MLSW_FLAG_NO_PERSISTENT). MLSW_ERR_ARG for a NULL handle or nsteps < 0;
+ * MLSW_ERR_CUDA if a launch fails. */
 int mlswlbm_step(mlsw_handle* h, long nsteps);
 
 /* Heights h_i = sum_k f_ki into out (host, n*nx*ny floats). Synchronises.

@@ -32,6 +32,13 @@ struct StepLaunch {
 };
 cudaError_t launch_step(const StepLaunch& a, cudaStream_t st);
 
+// D1Q3 lattices small enough for one CTA's shared memory run many steps in
+// one persistent launch: bytes of shared memory it needs (0: not possible
+// for this lattice type), and the launch, which reads a.fin and leaves the
+// state after nsteps steps in a.fout (ghost images included).
+size_t step_persistent_smem(int n, int lattice, int nx);
+cudaError_t launch_step_persistent(const StepLaunch& a, int nsteps, cudaStream_t st);
+
 // Tile shape of the step kernels (the padded layout covers whole tiles).
 int step_tile_cols(int lattice);
 int step_tile_rows(int n, int lattice);

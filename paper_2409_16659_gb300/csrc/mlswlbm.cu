@@ -29,6 +29,7 @@ struct mlsw_handle {
   long launches;
   mlsw::KShift sh;    // rest-population shift H_i (also in kp.H)
   int num_sms;
+  size_t psmem;       // D1Q3 persistent launch: shared memory bytes (0: not used)
   CUtensorMap map[2]; // D2Q9: tensor map of each buffer, box = one tile + halo
 };
 
@@ -396,6 +397,14 @@ int mlswlbm_create(const mlsw_params* p, const float* h_init, void* stream, mlsw
   }
   h->num_sms = sms > 0 ? sms : 1;
   h->nblk_diag = 2 * h->num_sms;
+  if (!(p->flags & MLSW_FLAG_NO_PERSISTENT)) {
+    int optin = 0;
+    const size_t need = mlsw::step_persistent_smem(n, p->lattice, p->nx);
+    if (need > 0 &&
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
+        need <= (size_t)optin)
+      h->psmem = need;
+  }
   bool ok = cudaMalloc(&h->f[0], h->flen * sizeof(float)) == cudaSuccess &&
             cudaMalloc(&h->f[1], h->flen * sizeof(float)) == cudaSuccess &&
             cudaMalloc(&h->hbuf, (size_t)n * ncell * sizeof(float)) == cudaSuccess &&
@@ -458,6 +467,20 @@ int mlswlbm_step(mlsw_handle* h, long nsteps) {
   a.status = h->status;
   a.sched = h->status + 1;
   a.num_sms = h->num_sms;
+  if (h->psmem) {
+    // whole lattice in one CTA: chunks of steps per launch
+    constexpr long kChunk = 16384;
+    for (long left = nsteps; left > 0;) {
+      const int chunk = (int)(left < kChunk ? left : kChunk);
+      a.fin = h->f[h->cur];
+      a.fout = h->f[h->cur ^ 1];
+      CU(mlsw::launch_step_persistent(a, chunk, h->stream));
+      h->launches += 1;
+      h->cur ^= 1;
+      left -= chunk;
+    }
+    return MLSW_OK;
+  }
   for (long s = 0; s < nsteps; ++s) {
     a.fin = h->f[h->cur];
     a.fout = h->f[h->cur ^ 1];

@@ -489,6 +489,52 @@ __global__ void __launch_bounds__(256, 2)
 }
 
 // ---------------------------------------------------------------------------
+// D1Q3 cell arithmetic shared by the tiled and the persistent kernels, so
+// both give the same bits.
+// ---------------------------------------------------------------------------
+// p_i of one cell from z deviations at x - 1, x, x + 1
+template <int N, bool W32>
+__device__ __forceinline__ void d1q3_pressures(const KParams& P, const float (&zw)[N],
+                                               const float (&zc)[N], const float (&ze)[N],
+                                               float (&p)[N]) {
+  float zd[N], gxz[N], gyz[N], lz[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const float e = ze[i] - zc[i], wv = zw[i] - zc[i];
+    zd[i] = zc[i];
+    gxz[i] = 0.5f * (e - wv);  // (1/cs^2) w_1 = 1/2
+    gyz[i] = 0.f;
+    lz[i] = e + wv;            // (2/cs^2) w_1 = 1
+  }
+  layer_pressures_dev<N, W32>(P, zd, gxz, gyz, lz, p);
+}
+
+// Force, collision with forcing, for one cell: fs[i][k] receives the
+// post-collision populations; f_old is read only when !TAU1. Returns true
+// when a height is not positive or a force not finite.
+template <int N, bool TAU1>
+__device__ __forceinline__ bool d1q3_collide_cell(const KParams& P, const float (&dd)[N],
+                                                  const float (&hh)[N], const float (&jx)[N],
+                                                  const float (&pw)[N], const float (&pc)[N],
+                                                  const float (&pe)[N], const float (&f_old)[N][3],
+                                                  float (&fs)[N][3]) {
+  float zero[N], Rx[N], Ry[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) zero[i] = 0.f;
+  friction<N>(P, hh, jx, zero, Rx, Ry);
+  bool bad = false;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const float gpx = 0.5f * ((pe[i] - pc[i]) - (pw[i] - pc[i]));
+    const float h = hh[i];
+    const float Fx = fmav(-h, gpx, Rx[i]);
+    bad |= !(h > 0.f) || !isfinite(Fx) || !isfinite(jx[i]);
+    collide<1, TAU1>(P, h, dd[i], jx[i], 0.f, Fx, 0.f, f_old[i], fs[i]);
+  }
+  return bad;
+}
+
+// ---------------------------------------------------------------------------
 // D1Q3: tile of TX cells, one cell per thread, plain loads (the padded
 // layout supplies the periodic images in x).
 // ---------------------------------------------------------------------------
@@ -526,35 +572,40 @@ __global__ void __launch_bounds__(TX)
     float z = 0.f;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      z += __ldg(fin + L.at(i * Q + 0, x, 0)) +
-           (__ldg(fin + L.at(i * Q + 1, x, 0)) + __ldg(fin + L.at(i * Q + 2, x, 0)));
+      const float f0 = __ldg(fin + L.at(i * Q + 0, x, 0));
+      const float f1 = __ldg(fin + L.at(i * Q + 1, x, 0));
+      const float f2 = __ldg(fin + L.at(i * Q + 2, x, 0));
+      z += f0 + (f1 + f2);
       zs[i][rc] = z;
     }
   }
   __syncthreads();
   for (int pc = tx; pc < PW; pc += TX) {
     const int rc = pc + 1;
-    float zd[N], gxz[N], gyz[N], lz[N], p[N];
+    float zw[N], zc[N], ze[N], p[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      const float c = zs[i][rc];
-      const float e = zs[i][rc + 1] - c, wv = zs[i][rc - 1] - c;
-      zd[i] = c;
-      gxz[i] = 0.5f * (e - wv);  // (1/cs^2) w_1 = 1/2
-      gyz[i] = 0.f;
-      lz[i] = e + wv;            // (2/cs^2) w_1 = 1
+      zw[i] = zs[i][rc - 1];
+      zc[i] = zs[i][rc];
+      ze[i] = zs[i][rc + 1];
     }
-    layer_pressures_dev<N, W32>(P, zd, gxz, gyz, lz, p);
+    d1q3_pressures<N, W32>(P, zw, zc, ze, p);
 #pragma unroll
     for (int i = 0; i < N; ++i) ps[i][pc] = p[i];
   }
   __syncthreads();
   const int gx = x0 + tx;
   if (gx >= nx) return;
-  float zero[N], Rx[N], Ry[N];
+  float pw[N], pc[N], pe[N], fo[N][Q], fs[N][Q];
 #pragma unroll
-  for (int i = 0; i < N; ++i) zero[i] = 0.f;
-  friction<N>(P, hh, jx, zero, Rx, Ry);
+  for (int i = 0; i < N; ++i) {
+    pw[i] = ps[i][tx];
+    pc[i] = ps[i][tx + 1];
+    pe[i] = ps[i][tx + 2];
+#pragma unroll
+    for (int k = 0; k < Q; ++k) fo[i][k] = TAU1 ? 0.f : fin[L.at(i * Q + k, gx, 0)];
+  }
+  const bool bad = d1q3_collide_cell<N, TAU1>(P, dd, hh, jx, pw, pc, pe, fo, fs);
   int dxs[3], xis[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -564,26 +615,108 @@ __global__ void __launch_bounds__(TX)
     dxs[c] = dx;
     xis[c] = P.tiny ? kNoImage : image_of(dx, nx);  // tiny lattices refresh ghosts apart
   }
-  bool bad = false;
 #pragma unroll
-  for (int i = 0; i < N; ++i) {
-    const float c = ps[i][tx + 1];
-    const float gpx = 0.5f * ((ps[i][tx + 2] - c) - (ps[i][tx] - c));
-    const float h = hh[i];
-    const float Fx = -h * gpx + Rx[i];
-    bad |= !(h > 0.f) || !isfinite(Fx) || !isfinite(jx[i]);
-    float fo[Q];
-    if (!TAU1) {
-#pragma unroll
-      for (int k = 0; k < Q; ++k) fo[k] = fin[L.at(i * Q + k, gx, 0)];
-    }
-    float fs[Q];
-    collide<1, TAU1>(P, h, dd[i], jx[i], 0.f, Fx, 0.f, fo, fs);
+  for (int i = 0; i < N; ++i)
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
       const int cxi = Lattice<1>::cx(k) + 1;
-      store_edge(fout + (long)(i * Q + k) * L.plane, L, dxs[cxi], 0, xis[cxi], kNoImage, fs[k]);
+      store_edge(fout + (long)(i * Q + k) * L.plane, L, dxs[cxi], 0, xis[cxi], kNoImage,
+                 fs[i][k]);
     }
+  if (bad) atomicOr(status, kStatusNonfinite);
+}
+
+// ---------------------------------------------------------------------------
+// D1Q3, persistent: one CTA holds the whole lattice in shared memory and
+// runs nsteps steps in one launch, with barriers between the phases of a
+// step instead of kernel launches. Shared memory (floats): two population
+// buffers [3N][nx], z [N][nx], p [N][nx]. The lattice is read from fin and
+// the final state written to fout (which may be fin), ghost images
+// included. Same cell arithmetic as step_d1q3_kernel.
+// ---------------------------------------------------------------------------
+constexpr int kD1PT = 256;
+
+template <int N, bool TAU1, bool W32>
+__global__ void __launch_bounds__(kD1PT)
+    step_d1q3_persistent(const float* fin, float* fout, const KParams P, int nsteps,
+                         int* __restrict__ status) {
+  constexpr int Q = 3;
+  extern __shared__ __align__(16) float sm[];
+  const Layout& L = P.L;
+  const int nx = P.nx, tid = threadIdx.x;
+  float* fa = sm;                     // current populations [i * Q + k][x]
+  float* fb = fa + 3 * N * nx;        // next populations
+  float* zsm = fb + 3 * N * nx;       // [i][x]
+  float* psm = zsm + N * nx;          // [i][x]
+  for (int t = tid; t < Q * N * nx; t += kD1PT) {
+    const int pl = t / nx, x = t - pl * nx;
+    fa[t] = fin[L.at(pl, x, 0)];
+  }
+  __syncthreads();
+  bool bad = false;
+  for (int s = 0; s < nsteps; ++s) {
+    // moments -> z
+    for (int x = tid; x < nx; x += kD1PT) {
+      float z = 0.f;
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        z += fa[(i * Q + 0) * nx + x] + (fa[(i * Q + 1) * nx + x] + fa[(i * Q + 2) * nx + x]);
+        zsm[i * nx + x] = z;
+      }
+    }
+    __syncthreads();
+    // pressures
+    for (int x = tid; x < nx; x += kD1PT) {
+      const int xw = x == 0 ? nx - 1 : x - 1, xe = x == nx - 1 ? 0 : x + 1;
+      float zw[N], zc[N], ze[N], p[N];
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        zw[i] = zsm[i * nx + xw];
+        zc[i] = zsm[i * nx + x];
+        ze[i] = zsm[i * nx + xe];
+      }
+      d1q3_pressures<N, W32>(P, zw, zc, ze, p);
+#pragma unroll
+      for (int i = 0; i < N; ++i) psm[i * nx + x] = p[i];
+    }
+    __syncthreads();
+    // force, collision, streaming into fb
+    for (int x = tid; x < nx; x += kD1PT) {
+      const int xw = x == 0 ? nx - 1 : x - 1, xe = x == nx - 1 ? 0 : x + 1;
+      float dd[N], hh[N], jx[N], pw[N], pc[N], pe[N], fo[N][Q], fs[N][Q];
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const float f0 = fa[(i * Q + 0) * nx + x], f1 = fa[(i * Q + 1) * nx + x];
+        const float f2 = fa[(i * Q + 2) * nx + x];
+        const float sum = f0 + (f1 + f2);
+        dd[i] = sum;
+        hh[i] = P.H[i] + sum;
+        jx[i] = f1 - f2;
+        fo[i][0] = f0;
+        fo[i][1] = f1;
+        fo[i][2] = f2;
+        pw[i] = psm[i * nx + xw];
+        pc[i] = psm[i * nx + x];
+        pe[i] = psm[i * nx + xe];
+      }
+      bad |= d1q3_collide_cell<N, TAU1>(P, dd, hh, jx, pw, pc, pe, fo, fs);
+      const int dst[3] = {x, xe, xw};  // c_k = 0, +1, -1
+#pragma unroll
+      for (int i = 0; i < N; ++i)
+#pragma unroll
+        for (int k = 0; k < Q; ++k) fb[(i * Q + k) * nx + dst[k]] = fs[i][k];
+    }
+    __syncthreads();
+    float* t = fa;
+    fa = fb;
+    fb = t;
+  }
+  // final state, real cells and the ghost images x in [-2, nx + 2)
+  for (int t = tid; t < Q * N * (nx + 4); t += kD1PT) {
+    const int pl = t / (nx + 4), x = t - pl * (nx + 4) - 2;
+    int sx = x % nx;
+    sx += sx < 0 ? nx : 0;
+    fout[L.at(pl, x, 0)] = fa[pl * nx + sx];
   }
   if (bad) atomicOr(status, kStatusNonfinite);
 }
@@ -643,6 +776,40 @@ static cudaError_t launch_n(const StepLaunch& a, cudaStream_t st) {
     step_d1q3_kernel<N, kD1TX, false, false><<<grid, kD1TX, 0, st>>>(a.fin, a.fout, a.P, a.status);
   }
   return cudaGetLastError();
+}
+
+size_t step_persistent_smem(int n, int lattice, int nx) {
+  if (lattice != 1 || n < 1 || n > kMaxLayers || nx < 1) return 0;
+  return (size_t)8 * n * nx * sizeof(float);
+}
+
+template <int N, bool TAU1, bool W32>
+static cudaError_t launch_d1p(const StepLaunch& a, int nsteps, cudaStream_t st) {
+  auto kern = step_d1q3_persistent<N, TAU1, W32>;
+  const size_t smem = step_persistent_smem(N, 1, a.P.nx);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<1, kD1PT, smem, st>>>(a.fin, a.fout, a.P, nsteps, a.status);
+  return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t launch_d1p_n(const StepLaunch& a, int nsteps, cudaStream_t st) {
+  const bool tau1 = (a.P.omega == 1.f);
+  const bool w32 = (a.P.nw == 3 && a.P.mw == 2);
+  if (tau1) return w32 ? launch_d1p<N, true, true>(a, nsteps, st) : launch_d1p<N, true, false>(a, nsteps, st);
+  return launch_d1p<N, false, false>(a, nsteps, st);
+}
+
+cudaError_t launch_step_persistent(const StepLaunch& a, int nsteps, cudaStream_t st) {
+  switch (a.P.n) {
+    case 1: return launch_d1p_n<1>(a, nsteps, st);
+    case 2: return launch_d1p_n<2>(a, nsteps, st);
+    case 3: return launch_d1p_n<3>(a, nsteps, st);
+    case 4: return launch_d1p_n<4>(a, nsteps, st);
+    case 5: return launch_d1p_n<5>(a, nsteps, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_step(const StepLaunch& a, cudaStream_t st) {

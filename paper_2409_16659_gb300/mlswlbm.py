@@ -20,6 +20,7 @@ MLSW_MAX_LAYERS = 5
 MLSW_D1Q3 = 1
 MLSW_D2Q9 = 2
 MLSW_FLAG_SKIP_STABILITY_CHECK = 1
+MLSW_FLAG_NO_PERSISTENT = 2
 
 MLSW_OK = 0
 MLSW_ERR_ARG = -1

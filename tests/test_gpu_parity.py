@@ -240,7 +240,14 @@ def test_torch_stream_binding_and_launch_count():
         a.step(40)
         b.step(40)
         assert np.array_equal(a.get_heights(), b.get_heights())
-        assert a.launch_count() == 1 + 40 + 1  # init (with ghost images), steps, read-out
+        # init (with ghost images), one persistent launch for the 40 steps of
+        # this one-CTA D1Q3 lattice, read-out
+        assert a.launch_count() == 1 + 1 + 1
+    q = dict(p, flags=B.MLSW_FLAG_NO_PERSISTENT)
+    with B.Solver(q, h0) as c:
+        c.step(40)
+        c.get_heights()
+        assert c.launch_count() == 1 + 40 + 1
 
 
 def test_pinned_host_heights_match_pageable():
@@ -269,3 +276,38 @@ def test_pinned_host_heights_match_pageable():
         with pytest.raises(B.MlswError):
             b.set_heights(pin_bad.numpy())
             b.get_heights(pin_out.numpy())
+
+
+PERSIST = [(1, 1.0, 512, 3), (2, 1.0, 512, 3), (3, 0.8, 37, 2), (4, 1.0, 1, 3), (5, 1.3, 2, 3),
+           (2, 1.0, 3, 2), (3, 1.0, 1000, 3)]
+
+
+@pytest.mark.parametrize("n,tau,nx,nw", PERSIST)
+def test_d1q3_persistent_matches_per_step_launches_bit_exact(n, tau, nx, nw):
+    """The one-CTA persistent D1Q3 kernel runs the same cell arithmetic as
+    the per-step kernel: states agree bit for bit, tiny and odd sizes
+    included, for tau = 1 and tau != 1."""
+    p = workloads.random_params(100 + n, n, B.MLSW_D1Q3, nx, 1, tau=tau)
+    p["nw"], p["mw"] = (3, 2) if nw == 3 else (4, 2)
+    h0 = workloads.random_heights(200 + n, p)
+    q = dict(p, flags=B.MLSW_FLAG_NO_PERSISTENT)
+    with B.Solver(p, h0) as a, B.Solver(q, h0) as b:
+        a.step(25)
+        b.step(25)
+        assert np.array_equal(a.get_state(), b.get_state())
+        a.step(1)
+        b.step(1)
+        assert np.array_equal(a.get_heights(), b.get_heights())
+        assert a.status() == B.MLSW_OK
+
+
+def test_d1q3_persistent_chunked_long_run():
+    """More steps than one persistent launch takes (16384): the chunks hand
+    the state over exactly."""
+    p = workloads.film2_d1q3_params(512)
+    h0 = workloads.film2_d1q3_heights(512)
+    q = dict(p, flags=B.MLSW_FLAG_NO_PERSISTENT)
+    with B.Solver(p, h0) as a, B.Solver(q, h0) as b:
+        a.step(16384 + 7)
+        b.step(16384 + 7)
+        assert np.array_equal(a.get_state(), b.get_state())
