@@ -18,6 +18,15 @@ The e2e figure goes through the public API with host buffers: every step
 uploads the heights from pinned memory (mlswlbm_set_heights), advances one
 step and reads the heights back (mlswlbm_get_heights).
 
+Two more workloads are reported beside the main line, under "workloads"
+(rank 0, after the timed region; --no-extra skips them):
+  * two-layer pseudo-2D film, D1Q3, 512 cells: time to solution of 10 000
+    steps through mlswlbm_step (one persistent launch holds the lattice on
+    chip) and heights read back, wall clock;
+  * three-layer lens field, D2Q9, 2048 x 2048, lenses of radius 200 (the
+    droplet/lens equilibrium workload): LSU/s over event-timed
+    back-to-back steps; its 2 x 906 MB working set exceeds the L2.
+
 Reference arm (--impl reference): the FP64 CPU oracle on the host cores, one
 oracle step per benchmark step on a 128 x 128 patch with the same recipe.
 Under torchrun only rank 0 runs it.
@@ -319,6 +328,8 @@ def run_own(args):
             "step_ms_p50": float(np.median(step_ms)), "step_ms_min": float(step_ms.min()),
             "status": B.mlswlbm_strerror(status),
         }
+        if not args.no_extra:
+            line["workloads"] = extra_workloads(B, torch)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_oracle_sample()
         print(json.dumps(line), flush=True)
@@ -326,6 +337,47 @@ def run_own(args):
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
     return 0
+
+
+def extra_workloads(B, torch):
+    """Time to solution of the D1Q3 film and LSU/s of the 2048^2 lens field."""
+    out = {}
+    p = workloads.film2_d1q3_params(512)
+    h0 = workloads.film2_d1q3_heights(512)
+    with B.Solver(p, h0) as s:
+        s.step(100)
+        torch.cuda.synchronize()
+        l0 = s.launch_count()
+        t0 = time.perf_counter()
+        s.step(10000)
+        h = s.get_heights()
+        t1 = time.perf_counter()
+        out["film2_d1q3_512"] = {
+            "steps": 10000, "ms_to_solution": 1e3 * (t1 - t0),
+            "steps_per_s": 10000 / (t1 - t0), "gpu_launches": int(s.launch_count() - l0),
+            "note": "mlswlbm_step(10000) + mlswlbm_get_heights, wall clock",
+            "finite": bool(np.isfinite(h).all())}
+    side, radius, steps = 2048, 200.0, 100
+    p = workloads.lens3_params(side, side, radius)
+    h0 = workloads.lens3_heights(side, side, radius)
+    st = torch.cuda.current_stream()
+    with B.Solver(p, h0, stream=st) as s:
+        s.step(5)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        s.step(steps)
+        e1.record(st)
+        torch.cuda.synchronize()
+        dt = e0.elapsed_time(e1) * 1e-3 / steps
+        lsu = 3 * side * side
+        peak, _ = hbm_peak()
+        out["lens3_d2q9_2048"] = {
+            "value": lsu / dt, "unit": UNIT, "ms_per_step": 1e3 * dt, "steps": steps,
+            "roofline_frac": BYTES_PER_LSU * lsu / dt / 1e9 / peak,
+            "l2": "back-to-back steps; 2 x 906 MB working set > 129 MB L2",
+            "status": B.mlswlbm_strerror(s.status())}
+    return out
 
 
 def run_profile(args):
@@ -351,6 +403,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the D1Q3 film and 2048^2 lens workloads")
     ap.add_argument("--profile", action="store_true",
                     help="only warm-up + --steps back-to-back steps (for ncu captures)")
     args = ap.parse_args()

@@ -33,9 +33,9 @@
  *         D2Q9: c = (0,0),(1,0),(1,1),(0,1),(-1,1),(-1,0),(-1,-1),(0,-1),(1,-1).
  *     A state is stored post-streaming: f[i][k] at cell x arrived from x - c_k.
  *   - Inside a handle the rest population of layer i is stored shifted by a
- *     per-layer constant H_i (f_0 - H_i; H_i = mid-range of the layer in
- *     h_init), which keeps the long-wave height differences representable
- *     in FP32. mlswlbm_get_state / mlswlbm_set_state convert to and from the
+ *     per-layer constant H_i (f_0 - H_i; H_i = median of the layer in
+ *     h_init), which keeps the long-wave height differences and the small
+ *     fluxes of precursor films representable in FP32. mlswlbm_get_state / mlswlbm_set_state convert to and from the
  *     true populations; mlswlbm_save_state / mlswlbm_load_state move the
  *     internal representation unchanged (bit-exact checkpoints).
  */

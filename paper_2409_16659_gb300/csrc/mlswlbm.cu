@@ -4,7 +4,9 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <new>
+#include <vector>
 
 #include "../../include/mlswlbm.h"
 #include "kernels.h"
@@ -362,9 +364,26 @@ int mlswlbm_create(const mlsw_params* p, const float* h_init, void* stream, mlsw
     hmax[i] = mx;
     hmean[i] = sum / (double)ncell;
     hst[i] = p->hstar;
-    // mid-range: independent of the order of the cells (so a translated
-    // field gets the same shift) and within the field's range
-    shift[i] = (float)(0.5 * (mn + mx));
+  }
+  // Shift H_i = median of the layer: independent of the order of the cells
+  // (a translated field gets the same shift) and close to most cells. The
+  // rest population of a cell at h is stored as h - H_i, so cells near H_i
+  // keep the small fluxes through them above FP32 rounding: in a nearly
+  // flat film the median is its mean level, in a droplet field the
+  // precursor that covers most of the layer.
+  {
+    std::vector<float> buf;
+    try {
+      buf.resize((size_t)ncell);
+    } catch (...) {
+      return MLSW_ERR_NOMEM;
+    }
+    for (int i = 0; i < n; ++i) {
+      std::copy(h_init + (long)i * ncell, h_init + (long)(i + 1) * ncell, buf.begin());
+      auto mid = buf.begin() + (ncell - 1) / 2;
+      std::nth_element(buf.begin(), mid, buf.end());
+      shift[i] = *mid;
+    }
   }
   if (!(p->flags & MLSW_FLAG_SKIP_STABILITY_CHECK)) {
     const double* states[4] = {hst, hmin, hmean, hmax};

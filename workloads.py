@@ -24,6 +24,28 @@ runs; these stand in for its two- and three-layer spinodal set-ups):
 A contact angle theta is turned into the one-layer spreading coefficients by
 Young's law, cos(theta) = 1 + S_{i1} / gamma_{i+1,i+2}; multi-layer
 coefficients S_{ik}, k >= 2, are zero as in the paper's three-layer runs.
+
+Droplet and lens equilibria (section "Droplet equilibria"; the paper gives
+no grid sizes, so these are stand-ins):
+  * sessile ridge, D1Q3: one layer, precursor h*, a circular-arc ridge of
+    base half-width a at contact angle theta0; S_01 = gamma (cos thetaY - 1)
+    so that Young's law gives thetaY;
+  * symmetric liquid lens, D1Q3: liquid one flat at thickness T1, liquid two
+    a lens of two equal arcs (opening angle theta0 above and below the far
+    level of the liquid-one surface) on its precursor h*; gamma_12 =
+    gamma_23 = gamma and S_11 = 2 gamma (cos thetaN - 1), every other S
+    zero, so that Neumann's law gives thetaN on both sides;
+  * three-layer lens field, D2Q9: layer 1 flat at 1.0, layer 2 flat at
+    0.3 r (deep enough for the lens to float), layer 3 four seeded lenses of
+    base radius r (12.5 cells at 128 x 128, 200 at 2048 x 2048) on its
+    precursor h* = 0.05; one tension gamma for all three liquids and
+    S_21 = 2 gamma (cos thetaN - 1), every other S zero (the substrate and
+    the lower liquids fully wet, so layers 1 and 2 stay flat films). The
+    tension is gamma = 0.125 / r (0.01 at r = 12.5): films a few tens of
+    cells thick with gamma = 0.01 carry capillary waves that the explicit
+    step does not damp, and scaling gamma with 1 / r keeps thickness times
+    tension, and so the step's stability, the same at every size; the
+    Neumann angles depend on tension ratios only.
 """
 import math
 
@@ -137,3 +159,98 @@ def single_mode_heights(p, h0, amps, mode, eps):
     for i in range(n):
         h[i] = h0[i] + eps * amps[i] * np.cos(ph)
     return h
+
+
+def cap_profile(dist, peak, base, theta):
+    """Height of a circular arc (a spherical cap in 2-D) of contact angle
+    theta (radians) whose top is `peak` above a flat `base` at distance
+    dist = 0; `base` outside the contact line."""
+    rc = (peak - base) / (1.0 - math.cos(theta))
+    inside = np.sqrt(np.maximum(rc * rc - np.asarray(dist, dtype=float) ** 2, 0.0))
+    return base + np.maximum(0.0, inside - rc * math.cos(theta))
+
+
+def drop1d_params(nx=128, theta_y_deg=20.0, gamma=0.01, hstar=0.1):
+    """One layer on D1Q3 whose Young angle is theta_y_deg."""
+    return dict(n=1, lattice=1, nx=int(nx), ny=1, tau=1.0, gamma=[gamma],
+                S=[[gamma * (math.cos(math.radians(theta_y_deg)) - 1.0)]],
+                mu=[1.0 / 6.0], beta=[1.0], nw=3, mw=2, hstar=hstar)
+
+
+def drop1d_heights(nx=128, theta0_deg=20.0, area=None, half_width=20.0, hstar=0.1):
+    """A circular-arc ridge centred in the box on the precursor h*. Either
+    its base half-width or its cross-section `area` (above h*) is given."""
+    th = math.radians(theta0_deg)
+    if area is not None:
+        rc = math.sqrt(area / (th - math.sin(th) * math.cos(th)))
+    else:
+        rc = half_width / math.sin(th)
+    x = np.arange(nx, dtype=float)
+    h = cap_profile(x - nx / 2.0, hstar + rc * (1.0 - math.cos(th)), hstar, th)
+    return h.reshape(1, 1, nx)
+
+
+def lens1d_params(nx=160, theta_n_deg=20.0, gamma=0.01, hstar=0.1):
+    """Two layers on D1Q3: liquid two forms a symmetric lens on liquid one."""
+    s11 = 2.0 * gamma * (math.cos(math.radians(theta_n_deg)) - 1.0)
+    return dict(n=2, lattice=1, nx=int(nx), ny=1, tau=1.0, gamma=[gamma, gamma],
+                S=[[0.0, 0.0], [s11]], mu=[1.0 / 6.0, 1.0 / 6.0], beta=[1.0, 1.0],
+                nw=3, mw=2, hstar=hstar)
+
+
+def lens1d_heights(nx=160, theta0_deg=20.0, half_width=20.0, t1=6.0, hstar=0.1):
+    """Liquid one flat at t1 with the lower arc carved out, liquid two the
+    lens (both arcs) on its precursor."""
+    th = math.radians(theta0_deg)
+    rc = half_width / math.sin(th)
+    x = np.arange(nx, dtype=float)
+    arc = cap_profile(x - nx / 2.0, rc * (1.0 - math.cos(th)), 0.0, th)
+    return np.stack([t1 - arc, hstar + 2.0 * arc]).reshape(2, 1, nx)
+
+
+def lens3_params(nx=128, ny=128, radius=12.5, theta_n_deg=20.0, hstar=0.05):
+    """Three layers on D2Q9: liquid three forms symmetric lenses of base
+    radius `radius` on liquid two; only S_21 is non-zero."""
+    gamma = 0.125 / radius
+    s21 = 2.0 * gamma * (math.cos(math.radians(theta_n_deg)) - 1.0)
+    return dict(n=3, lattice=2, nx=int(nx), ny=int(ny), tau=1.0,
+                gamma=[gamma, gamma, gamma], S=[[0.0, 0.0, 0.0], [0.0, 0.0], [s21]],
+                mu=[1.0 / 6.0, 2.0 / 6.0, 4.0 / 6.0], beta=[1.0, 1.0, 1.0],
+                nw=3, mw=2, hstar=hstar)
+
+
+def lens3_centres(nx, ny, radius, count=4, seed=4):
+    """Seeded lens centres at least 2.6 radii apart (periodic distance)."""
+    rng = np.random.default_rng(seed)
+    centres = []
+    for _ in range(10000):
+        if len(centres) == count:
+            break
+        c = rng.uniform(0.0, 1.0, 2) * (nx, ny)
+        ok = True
+        for d in centres:
+            dx = abs(c[0] - d[0]); dx = min(dx, nx - dx)
+            dy = abs(c[1] - d[1]); dy = min(dy, ny - dy)
+            ok = ok and math.hypot(dx, dy) >= 2.6 * radius
+        if ok:
+            centres.append(c)
+    if len(centres) < count:
+        raise ValueError("lenses do not fit the box")
+    return np.array(centres)
+
+
+def lens3_heights(nx=128, ny=128, radius=12.5, theta0_deg=20.0, hstar=0.05, seed=4):
+    """Layer 1 flat at 1, layer 2 flat at 0.3 r minus the lower arcs, layer 3
+    the lenses (both arcs) on the precursor h*; heights [3][ny][nx]."""
+    th = math.radians(theta0_deg)
+    rc = radius / math.sin(th)
+    depth = rc * (1.0 - math.cos(th))
+    x = np.arange(nx, dtype=float)[None, :]
+    y = np.arange(ny, dtype=float)[:, None]
+    arc = np.zeros((ny, nx))
+    for cx, cy in lens3_centres(nx, ny, radius, seed=seed):
+        dx = np.abs(x - cx); dx = np.minimum(dx, nx - dx)
+        dy = np.abs(y - cy); dy = np.minimum(dy, ny - dy)
+        arc = np.maximum(arc, cap_profile(np.hypot(dx, dy), depth, 0.0, th))
+    t2 = 0.3 * radius
+    return np.stack([np.ones((ny, nx)), t2 - arc, hstar + 2.0 * arc])
