@@ -243,6 +243,62 @@ int mlswlbm_friction_eval(const mlsw_params* p, long ncell, const float* h,
 int mlswlbm_diagnostics_noalloc(const mlsw_params* p, const float* f, const float* H,
                                 double* out, void* stream);
 
+/*
+ * ------------------------------------------------------------------------
+ * Batches: many independent D2Q9 lattices (e.g. the instances of a
+ * stability or equilibrium sweep: layer counts, sizes and parameters may all
+ * differ) advanced together. One step of a batch is one persistent kernel
+ * launch per group of instances sharing the layer count, the kernel mode
+ * (tau = 1 or not, exponents (3, 2), spreading only between neighbouring
+ * interfaces) and the tile height; the groups' launches of a step are
+ * captured once in a CUDA graph and replayed. Each instance is stepped with
+ * exactly the arithmetic of mlswlbm_step.
+ * ------------------------------------------------------------------------
+ */
+typedef struct mlsw_batch mlsw_batch;
+
+/* batch flags */
+#define MLSW_BATCH_TILE8 1    /* 8-row tiles for every instance (default: 16 rows for n <= 3) */
+#define MLSW_BATCH_AUTOTUNE 2 /* at create, time 8- and 16-row tiles for every class of
+                                 instances with the same n, kernel mode and size (n <= 3)
+                                 and keep the faster; the states are then reset to h_init */
+
+/* Creates a batch of count >= 1 lattices: params[j] and h_init[j] (host,
+ * [n_j][ny_j][nx_j]) as for mlswlbm_create, every lattice D2Q9 (else
+ * MLSW_ERR_UNSUPPORTED). Errors of an instance are those of mlswlbm_create.
+ * One device allocation holds all population buffers. On failure *out is
+ * NULL and nothing is leaked. */
+int mlswlbm_batch_create(int count, const mlsw_params* params, const float* const* h_init,
+                         int flags, void* stream, mlsw_batch** out);
+
+/* Enqueues nsteps >= 0 steps of every instance; asynchronous. */
+int mlswlbm_batch_step(mlsw_batch* b, long nsteps);
+
+/* Heights of instance index (host, [n][ny][nx]); synchronises; status as
+ * mlswlbm_get_heights (for the whole batch). MLSW_ERR_ARG for a bad index. */
+int mlswlbm_batch_get_heights(mlsw_batch* b, int index, float* out);
+
+/* One Fourier mode of every layer of every instance:
+ * out[2 (j MLSW_MAX_LAYERS + i) + 0 / 1] = Re / Im of
+ * sum_{x,y} h_i(x, y) exp(-2 pi i (kx[j] x / nx_j + ky[j] y / ny_j)),
+ * zero for i >= n_j. kx, ky: count host ints; out: 2 MLSW_MAX_LAYERS count
+ * host doubles. Synchronises; status as mlswlbm_get_heights. */
+int mlswlbm_batch_modes(mlsw_batch* b, const int* kx, const int* ky, double* out);
+
+/* MLSW_OK, MLSW_ERR_NONFINITE or MLSW_ERR_TIMEOUT for the whole batch since
+ * create or the last query (then cleared); synchronises. */
+int mlswlbm_batch_status(mlsw_batch* b);
+
+/* Tile rows (8 or 16) that instance index runs with, or MLSW_ERR_ARG. */
+int mlswlbm_batch_tile_rows(const mlsw_batch* b, int index);
+
+/* Kernel launches issued since create (graph replays counted by the
+ * kernels they contain), and groups (launches per step). */
+long mlswlbm_batch_launch_count(const mlsw_batch* b);
+int mlswlbm_batch_groups(const mlsw_batch* b);
+
+void mlswlbm_batch_destroy(mlsw_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -422,3 +422,85 @@ cudaError_t launch_friction_eval(const KParams& P, long ncell, const float* h, c
 }
 
 }  // namespace mlsw
+
+namespace mlsw {
+
+// ---------------------------------------------------------------------------
+// batches: one Fourier mode of every layer of every instance,
+//   hhat_i(q) = sum_x h_i(x) exp(-2 pi i (kx x / nx + ky y / ny)),
+// one CTA per (instance, layer); the phase is formed from exact integers.
+// ---------------------------------------------------------------------------
+constexpr int kModeThreads = 256;
+
+__global__ void __launch_bounds__(kModeThreads)
+    batch_mode_kernel(const BatchInst* __restrict__ inst, int cur, const int* __restrict__ kx,
+                      const int* __restrict__ ky, double* __restrict__ out) {
+  const int j = blockIdx.x / kMaxLayers, i = blockIdx.x - j * kMaxLayers;
+  const BatchInst& b = inst[j];
+  const KParams& P = b.P;
+  __shared__ double red[2][kModeThreads / 32];
+  if (i >= P.n) {
+    if (threadIdx.x == 0) {
+      out[2 * blockIdx.x] = 0.0;
+      out[2 * blockIdx.x + 1] = 0.0;
+    }
+    return;
+  }
+  const Layout& L = P.L;
+  const float* __restrict__ f = b.f[cur];
+  const int nx = P.nx, ny = P.ny;
+  const long ncell = (long)nx * ny;
+  const long qx = ((long)kx[j] % nx + nx) % nx, qy = ((long)ky[j] % ny + ny) % ny;
+  double re = 0.0, im = 0.0;
+  for (long c = threadIdx.x; c < ncell; c += kModeThreads) {
+    const int y = (int)(c / nx), x = (int)(c - (long)y * nx);
+    const float* src = f + L.at(i * 9, x, y);
+    float d = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) d += src[(long)k * L.plane];
+    const double h = (double)(P.H[i] + d);
+    // phase / (2 pi) = m / (nx ny), m exact
+    const long m = ((qx * x) % nx * ny + (qy * y) % ny * nx) % ncell;
+    float sn, cs;
+    sincospif(2.f * (float)((double)m / (double)ncell), &sn, &cs);
+    re += h * (double)cs;
+    im -= h * (double)sn;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    re += __shfl_down_sync(0xffffffffu, re, o);
+    im += __shfl_down_sync(0xffffffffu, im, o);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][wid] = re;
+    red[1][wid] = im;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, bb = 0.0;
+    for (int w = 0; w < kModeThreads / 32; ++w) {
+      a += red[0][w];
+      bb += red[1][w];
+    }
+    out[2 * blockIdx.x] = a;
+    out[2 * blockIdx.x + 1] = bb;
+  }
+}
+
+cudaError_t launch_batch_modes(const BatchInst* inst, int count, int cur, const int* kx,
+                               const int* ky, double* out, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  batch_mode_kernel<<<count * kMaxLayers, kModeThreads, 0, st>>>(inst, cur, kx, ky, out);
+  return cudaGetLastError();
+}
+
+// heights of one instance of a batch (layout of its buffers)
+cudaError_t launch_batch_heights(const BatchInst* inst_host, int cur, float* h, cudaStream_t st) {
+  return launch_heights(9, inst_host->P.n, inst_host->P.L, inst_host->f[cur],
+                        KShift{{inst_host->P.H[0], inst_host->P.H[1], inst_host->P.H[2],
+                                inst_host->P.H[3], inst_host->P.H[4]}},
+                        h, st);
+}
+
+}  // namespace mlsw

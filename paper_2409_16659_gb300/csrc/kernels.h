@@ -39,6 +39,52 @@ cudaError_t launch_step(const StepLaunch& a, cudaStream_t st);
 size_t step_persistent_smem(int n, int lattice, int nx);
 cudaError_t launch_step_persistent(const StepLaunch& a, int nsteps, cudaStream_t st);
 
+// ---------------------------------------------------------------------------
+// Batches: many independent D2Q9 lattices stepped by one persistent launch
+// per group of instances that share n, kernel mode and tile height.
+// ---------------------------------------------------------------------------
+// Tile heights a batch can use: variant 0 = 16 rows with two rows per
+// thread (n <= 3 only), variant 1 = 8 rows with one row per thread.
+constexpr int kBatchVariants = 2;
+__host__ __device__ constexpr int batch_variant(int rows_per_thread) {
+  return rows_per_thread == 2 ? 0 : 1;
+}
+__host__ __device__ constexpr int batch_tile_rows(int variant) { return variant == 0 ? 16 : 8; }
+
+// Device descriptor of one instance (aligned as its tensor maps require).
+struct BatchInst {
+  CUtensorMap map[kBatchVariants][2];  // [variant][input buffer]: box of one tile + halo
+  KParams P;
+  float* f[2];  // population buffers
+  int ntx;      // tile columns (tiles are 32 cells wide)
+};
+
+// Kernel mode of a parameter set: 0 general, 1 tau = 1, 2 fast (tau = 1,
+// exponents (3, 2), spreading only between neighbouring interfaces).
+int step_mode(const KParams& P);
+
+// One batch step of the instances of one group: tiles of table (device,
+// ntiles entries of (instance, tile)), buffers cur -> cur ^ 1.
+struct BatchLaunch {
+  int n, mode, variant;
+  const BatchInst* inst;
+  const int2* table;
+  int ntiles, cur;
+  int* status;
+  int* sched;  // two zero-initialised counters of this group
+  int num_sms;
+};
+cudaError_t launch_batch_step(const BatchLaunch& a, cudaStream_t st);
+
+// out[2 (j kMaxLayers + i) + {0, 1}] = real and imaginary part of
+// sum_x h_i(x) exp(-2 pi i (kx[j] x / nx + ky[j] y / ny)) for every instance
+// j < count and layer i (zero for i >= n_j); kx, ky device arrays.
+cudaError_t launch_batch_modes(const BatchInst* inst, int count, int cur, const int* kx,
+                               const int* ky, double* out, cudaStream_t st);
+
+// Heights [n][ny][nx] of one instance (its host descriptor) from buffer cur.
+cudaError_t launch_batch_heights(const BatchInst* inst_host, int cur, float* h, cudaStream_t st);
+
 // Tile shape of the step kernels (the padded layout covers whole tiles).
 int step_tile_cols(int lattice);
 int step_tile_rows(int n, int lattice);

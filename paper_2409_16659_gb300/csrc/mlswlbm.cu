@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/mlswlbm.h"
+#include "host.h"
 #include "kernels.h"
 #include "physics.cuh"
 
@@ -35,7 +36,7 @@ struct mlsw_handle {
   CUtensorMap map[2]; // D2Q9: tensor map of each buffer, box = one tile + halo
 };
 
-namespace {
+namespace mlsw_host {
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 
@@ -205,13 +206,13 @@ EncodeTiledFn encode_fn() {
 
 // 3-D map (x: pitch, y: rows, z: planes) whose box is one D2Q9 tile with
 // its halo: 40 x (TY + 4) x all planes.
-bool make_tile_map(CUtensorMap* m, float* base, const mlsw::Layout& L, int nplanes, int ty) {
+bool make_tile_map(CUtensorMap* m, float* base, const mlsw::Layout& L, int nplanes, int box_cols,
+                   int box_rows) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[3] = {(cuuint64_t)L.pitch, (cuuint64_t)L.rows, (cuuint64_t)nplanes};
   cuuint64_t strides[2] = {(cuuint64_t)L.pitch * 4, (cuuint64_t)L.plane * 4};
-  cuuint32_t box[3] = {(cuuint32_t)(mlsw::step_tile_cols(MLSW_D2Q9) + 8), (cuuint32_t)(ty + 4),
-                       (cuuint32_t)nplanes};
+  cuuint32_t box[3] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows, (cuuint32_t)nplanes};
   cuuint32_t es[3] = {1, 1, 1};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -237,19 +238,80 @@ cudaError_t copy_planes(mlsw_handle* h, float* host, const float* dev, bool to_h
   return cudaSuccess;
 }
 
-void set_shift(mlsw_handle* h, const float* H) {
+void set_shift(KParams& kp, mlsw::KShift& sh, int n, const float* H) {
   for (int i = 0; i < mlsw::kMaxLayers; ++i) {
-    const float v = (i < h->p.n_layers) ? H[i] : 0.f;
-    h->sh.H[i] = v;
-    h->kp.H[i] = v;
+    const float v = (i < n) ? H[i] : 0.f;
+    sh.H[i] = v;
+    kp.H[i] = v;
   }
   // reference thickness between interfaces l < m, summed in double
   for (int l = 0; l <= mlsw::kMaxLayers; ++l)
     for (int m = 0; m <= mlsw::kMaxLayers; ++m) {
       double acc = 0.0;
-      for (int j = l + 1; j <= m; ++j) acc += (double)h->sh.H[j - 1];
-      h->kp.Hsum[l][m] = (float)acc;
+      for (int j = l + 1; j <= m; ++j) acc += (double)sh.H[j - 1];
+      kp.Hsum[l][m] = (float)acc;
     }
+}
+
+void set_shift(mlsw_handle* h, const float* H) { set_shift(h->kp, h->sh, h->p.n_layers, H); }
+
+int prepare_instance(const mlsw_params& p, const float* h_init, KParams& kp, mlsw::KShift& sh) {
+  int rc = mlswlbm_check_params(&p);
+  if (rc != MLSW_OK) return rc;
+  if (!h_init) return MLSW_ERR_ARG;
+  rc = check_heights(p, h_init);
+  if (rc != MLSW_OK) return rc;
+  const int n = p.n_layers;
+  const long ncell = (long)p.nx * p.ny;
+
+  double hmin[MLSW_MAX_LAYERS], hmax[MLSW_MAX_LAYERS], hmean[MLSW_MAX_LAYERS],
+      hst[MLSW_MAX_LAYERS];
+  float shift[MLSW_MAX_LAYERS];
+  for (int i = 0; i < n; ++i) {
+    double mn = INFINITY, mx = -INFINITY, sum = 0.0;
+    for (long c = 0; c < ncell; ++c) {
+      const double v = h_init[(long)i * ncell + c];
+      mn = std::fmin(mn, v);
+      mx = std::fmax(mx, v);
+      sum += v;
+    }
+    hmin[i] = mn;
+    hmax[i] = mx;
+    hmean[i] = sum / (double)ncell;
+    hst[i] = p.hstar;
+  }
+  // Shift H_i = median of the layer: independent of the order of the cells
+  // (a translated field gets the same shift) and close to most cells. The
+  // rest population of a cell at h is stored as h - H_i, so cells near H_i
+  // keep the small fluxes through them above FP32 rounding: in a nearly
+  // flat film the median is its mean level, in a droplet field the
+  // precursor that covers most of the layer.
+  {
+    std::vector<float> buf;
+    try {
+      buf.resize((size_t)ncell);
+    } catch (...) {
+      return MLSW_ERR_NOMEM;
+    }
+    for (int i = 0; i < n; ++i) {
+      std::copy(h_init + (long)i * ncell, h_init + (long)(i + 1) * ncell, buf.begin());
+      auto mid = buf.begin() + (ncell - 1) / 2;
+      std::nth_element(buf.begin(), mid, buf.end());
+      shift[i] = *mid;
+    }
+  }
+  if (!(p.flags & MLSW_FLAG_SKIP_STABILITY_CHECK)) {
+    const double* states[4] = {hst, hmin, hmean, hmax};
+    for (const double* s : states)
+      if (!(spectral_radius_I_plus_K(p, s) < 1.0)) return MLSW_ERR_UNSTABLE;
+  }
+  kp = make_kparams(p);
+  kp.L = make_layout(p);
+  // the step kernels address a layer's planes with 32-bit offsets
+  if ((double)kp.L.plane * Qof(p.lattice) >= 2147483647.0) return MLSW_ERR_UNSUPPORTED;
+  set_ghost_tables(kp, p);
+  set_shift(kp, sh, n, shift);
+  return MLSW_OK;
 }
 
 // The address at which kernels on the current device can read or write a
@@ -265,7 +327,9 @@ const void* mapped_host_ptr(const void* p) {
   return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
-}  // namespace
+}  // namespace mlsw_host
+
+using namespace mlsw_host;
 
 extern "C" {
 
@@ -341,73 +405,25 @@ void mlswlbm_destroy(mlsw_handle* h) {
 int mlswlbm_create(const mlsw_params* p, const float* h_init, void* stream, mlsw_handle** out) {
   if (!out) return MLSW_ERR_ARG;
   *out = nullptr;
-  int rc = mlswlbm_check_params(p);
-  if (rc != MLSW_OK) return rc;
-  if (!h_init) return MLSW_ERR_ARG;
-  rc = check_heights(*p, h_init);
-  if (rc != MLSW_OK) return rc;
+  if (!p) return MLSW_ERR_ARG;
+  KParams kp;
+  mlsw::KShift sh;
+  const int rc0 = prepare_instance(*p, h_init, kp, sh);
+  if (rc0 != MLSW_OK) return rc0;
   const int n = p->n_layers;
   const long ncell = (long)p->nx * p->ny;
-
-  double hmin[MLSW_MAX_LAYERS], hmax[MLSW_MAX_LAYERS], hmean[MLSW_MAX_LAYERS],
-      hst[MLSW_MAX_LAYERS];
-  float shift[MLSW_MAX_LAYERS];
-  for (int i = 0; i < n; ++i) {
-    double mn = INFINITY, mx = -INFINITY, sum = 0.0;
-    for (long c = 0; c < ncell; ++c) {
-      const double v = h_init[(long)i * ncell + c];
-      mn = std::fmin(mn, v);
-      mx = std::fmax(mx, v);
-      sum += v;
-    }
-    hmin[i] = mn;
-    hmax[i] = mx;
-    hmean[i] = sum / (double)ncell;
-    hst[i] = p->hstar;
-  }
-  // Shift H_i = median of the layer: independent of the order of the cells
-  // (a translated field gets the same shift) and close to most cells. The
-  // rest population of a cell at h is stored as h - H_i, so cells near H_i
-  // keep the small fluxes through them above FP32 rounding: in a nearly
-  // flat film the median is its mean level, in a droplet field the
-  // precursor that covers most of the layer.
-  {
-    std::vector<float> buf;
-    try {
-      buf.resize((size_t)ncell);
-    } catch (...) {
-      return MLSW_ERR_NOMEM;
-    }
-    for (int i = 0; i < n; ++i) {
-      std::copy(h_init + (long)i * ncell, h_init + (long)(i + 1) * ncell, buf.begin());
-      auto mid = buf.begin() + (ncell - 1) / 2;
-      std::nth_element(buf.begin(), mid, buf.end());
-      shift[i] = *mid;
-    }
-  }
-  if (!(p->flags & MLSW_FLAG_SKIP_STABILITY_CHECK)) {
-    const double* states[4] = {hst, hmin, hmean, hmax};
-    for (const double* s : states)
-      if (!(spectral_radius_I_plus_K(*p, s) < 1.0)) return MLSW_ERR_UNSTABLE;
-  }
+  int rc = MLSW_OK;
 
   mlsw_handle* h = new (std::nothrow) mlsw_handle;
   if (!h) return MLSW_ERR_NOMEM;
   std::memset(h, 0, sizeof(*h));
   h->p = *p;
-  h->kp = make_kparams(*p);
+  h->kp = kp;
+  h->sh = sh;
   h->Q = Qof(p->lattice);
   h->ncell = ncell;
-  h->kp.L = make_layout(*p);
-  // the step kernels address a layer's planes with 32-bit offsets
-  if ((double)h->kp.L.plane * h->Q >= 2147483647.0) {
-    delete h;
-    return MLSW_ERR_UNSUPPORTED;
-  }
-  set_ghost_tables(h->kp, *p);
   h->flen = (size_t)n * h->Q * h->kp.L.plane;
   h->stream = (cudaStream_t)stream;
-  set_shift(h, shift);
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
@@ -445,9 +461,10 @@ int mlswlbm_create(const mlsw_params* p, const float* h_init, void* stream, mlsw
     return MLSW_ERR_CUDA;
   }
   if (p->lattice == MLSW_D2Q9) {
-    const int ty = mlsw::step_tile_rows(n, p->lattice);
-    if (!make_tile_map(&h->map[0], h->f[0], h->kp.L, n * h->Q, ty) ||
-        !make_tile_map(&h->map[1], h->f[1], h->kp.L, n * h->Q, ty)) {
+    const int bc = mlsw::step_tile_cols(p->lattice) + 8;
+    const int br = mlsw::step_tile_rows(n, p->lattice) + 4;
+    if (!make_tile_map(&h->map[0], h->f[0], h->kp.L, n * h->Q, bc, br) ||
+        !make_tile_map(&h->map[1], h->f[1], h->kp.L, n * h->Q, bc, br)) {
       mlswlbm_destroy(h);
       return MLSW_ERR_CUDA;
     }

@@ -162,10 +162,10 @@ template <> struct Lanes<f2> {
 // barrier waits. With tau = 1 the next tile's copy is issued as soon as the
 // moments are formed and lands while this tile is finished.
 // ---------------------------------------------------------------------------
-template <int N>
+template <int N, int RPT_ = (N <= 3 ? 2 : 1)>
 struct D2Tile {
   static constexpr int Q = 9, PN = N * Q, TX = 32;
-  static constexpr int TY = N <= 3 ? 16 : 8, NT = 256, BY = NT / 32, RPT = TY / BY;
+  static constexpr int NT = 256, BY = NT / 32, RPT = RPT_, TY = BY * RPT;
   static constexpr int BW = TX + 8, BH = TY + 4, STAGE = PN * BH * BW;
   static constexpr int RW = TX + 4, RH = TY + 4, PW = TX + 2, PH = TY + 2;
   static constexpr int NHALO = 4 * RW + 4 * TY;
@@ -186,12 +186,45 @@ struct D2Tile {
 // spreading coefficients only between neighbouring interfaces).
 enum StepMode { kGeneral = 0, kTau1 = 1, kFast = 2 };
 
-template <int N, int MODE>
-__global__ void __launch_bounds__(256, 2)
-    step_d2q9_tma(const __grid_constant__ CUtensorMap fin_map, float* __restrict__ fout,
-                  const KParams P, int* __restrict__ status, int* __restrict__ sched) {
+// One tile of work: its parameters, the tensor map of its input buffer, its
+// output buffer and its position in the tile grid of its lattice.
+struct TileRef {
+  const KParams* P;
+  const CUtensorMap* map;
+  float* fout;
+  int bx, by;
+};
+
+// Tiles of one lattice (the single-solver kernel).
+struct SingleTiles {
+  const KParams* P;
+  const CUtensorMap* map;
+  float* fout;
+  int ntx, ntiles;
+  __device__ TileRef operator()(int t) const { return {P, map, fout, t % ntx, t / ntx}; }
+  __device__ void prefetch() const { tma_prefetch_desc(map); }
+};
+
+// Tiles of many lattices (a batch): table[t] = (instance, tile of that
+// instance); every instance steps from buffer cur to cur ^ 1.
+struct BatchTiles {
+  const BatchInst* inst;
+  const int2* table;
+  int cur, ntiles, variant;  // variant: tensor-map set of this tile height
+  __device__ TileRef operator()(int t) const {
+    const int2 e = table[t];
+    const BatchInst& b = inst[e.x];
+    return {&b.P, &b.map[variant][cur], b.f[cur ^ 1], e.y % b.ntx, e.y / b.ntx};
+  }
+  __device__ void prefetch() const {}
+};
+
+// The persistent tile loop of the D2Q9 step, for any source of tiles.
+template <int N, int MODE, int RPT_, class Tiles>
+__device__ __forceinline__ void d2q9_tile_loop(const Tiles& tiles, int* __restrict__ status,
+                                               int* __restrict__ sched) {
   constexpr bool TAU1 = MODE != kGeneral, W32 = MODE == kFast, NN = MODE == kFast;
-  using Tl = D2Tile<N>;
+  using Tl = D2Tile<N, RPT_>;
   constexpr int Q = 9, TX = Tl::TX, TY = Tl::TY, BY = Tl::BY, RPT = Tl::RPT;
   constexpr int BW = Tl::BW, BH = Tl::BH, RW = Tl::RW, RH = Tl::RH, PW = Tl::PW, PH = Tl::PH;
   // a thread's two tile rows (iy, iy + BY) are evaluated as one FP32x2 pair
@@ -208,16 +241,14 @@ __global__ void __launch_bounds__(256, 2)
   __shared__ int next_tile;
 
   const int tid = threadIdx.x;
-  const Layout& L = P.L;
-  const int nx = P.nx, ny = P.ny;
-  const int ntx = (nx + TX - 1) / TX, nty = (ny + TY - 1) / TY, ntiles = ntx * nty;
+  const int ntiles = tiles.ntiles;
 
   auto issue = [&](int t) {
-    const int bx = t % ntx, by = t / ntx;
+    const TileRef r = tiles(t);
     fence_proxy_async_smem();
     mbar_arrive_expect_tx(bar, (uint32_t)Tl::kStageBytes);
     // box origin: real (x0 - 4, y0 - 2) = padded (x0, y0) since gx = 4, gy = 2
-    tma_load_3d(stage, &fin_map, bar, bx * TX, by * TY, 0);
+    tma_load_3d(stage, r.map, bar, r.bx * TX, r.by * TY, 0);
   };
   auto draw_next = [&]() {
     const int nt = (int)gridDim.x + atomicAdd(sched, 1);
@@ -247,12 +278,11 @@ __global__ void __launch_bounds__(256, 2)
   }
   __syncthreads();
   if (tid == 0) {
-    tma_prefetch_desc(&fin_map);
+    tiles.prefetch();
     if ((int)blockIdx.x < ntiles) issue(blockIdx.x);
   }
 
   const int ix = tid % TX, iyb = tid / TX;  // tile cells (ix, iyb + lane * BY)
-  const long lplane = (long)Q * L.plane;    // floats per layer
   bool bad = false;
   uint32_t parity = 0;
   // Tiles: the first one is blockIdx.x, later ones come from a global
@@ -260,7 +290,13 @@ __global__ void __launch_bounds__(256, 2)
   // The last CTA to finish resets the counters for the next launch.
   for (int t = blockIdx.x; t < ntiles; parity ^= 1u) {
     const bool timed_out = !mbar_wait_bounded(bar, parity);
-    const int x0 = (t % ntx) * TX, y0 = (t / ntx) * TY;
+    const TileRef tr = tiles(t);
+    const KParams& P = *tr.P;
+    const Layout& L = P.L;
+    const int nx = P.nx, ny = P.ny;
+    const long lplane = (long)Q * L.plane;  // floats per layer
+    float* __restrict__ fout = tr.fout;
+    const int x0 = tr.bx * TX, y0 = tr.by * TY;
 
     // ---- M. moments: deviations z on the two-ring region, J on the tile ----
     {
@@ -486,6 +522,27 @@ __global__ void __launch_bounds__(256, 2)
     sched[0] = 0;  // every CTA has drawn its last tile
     sched[1] = 0;
   }
+}
+
+template <int N, int MODE>
+__global__ void __launch_bounds__(256, 2)
+    step_d2q9_tma(const __grid_constant__ CUtensorMap fin_map, float* __restrict__ fout,
+                  const __grid_constant__ KParams P, int* __restrict__ status,
+                  int* __restrict__ sched) {
+  using Tl = D2Tile<N>;
+  const int ntx = (P.nx + Tl::TX - 1) / Tl::TX, nty = (P.ny + Tl::TY - 1) / Tl::TY;
+  const SingleTiles tiles{&P, &fin_map, fout, ntx, ntx * nty};
+  d2q9_tile_loop<N, MODE, Tl::RPT>(tiles, status, sched);
+}
+
+// One step of every instance of a batch group (same n, mode and tile rows):
+// one persistent launch over the group's tile table.
+template <int N, int MODE, int RPT>
+__global__ void __launch_bounds__(256, 2)
+    step_d2q9_batch(const BatchInst* __restrict__ inst, const int2* __restrict__ table, int ntiles,
+                    int cur, int* __restrict__ status, int* __restrict__ sched) {
+  const BatchTiles tiles{inst, table, cur, ntiles, batch_variant(RPT)};
+  d2q9_tile_loop<N, MODE, RPT>(tiles, status, sched);
 }
 
 // ---------------------------------------------------------------------------
@@ -754,17 +811,81 @@ static cudaError_t launch_d2(const StepLaunch& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+int step_mode(const KParams& P) {
+  if (P.omega != 1.f) return kGeneral;
+  const bool w32 = (P.nw == 3 && P.mw == 2);
+  bool nn = true;  // spreading coefficients only between neighbouring interfaces
+  for (int l = 0; l < P.n; ++l)
+    for (int k = 2; k <= P.n - l; ++k) nn = nn && (P.S[l][k - 1] == 0.f);
+  return (w32 && nn) ? kFast : kTau1;
+}
+
+// batch kernels: dynamic shared memory and occupancy, once per device and
+// instantiation
+template <int N, int MODE, int RPT>
+static cudaError_t launch_batch_nmr(const BatchLaunch& a, cudaStream_t st) {
+  using T = D2Tile<N, RPT>;
+  auto kern = step_d2q9_batch<N, MODE, RPT>;
+  static unsigned long long configured = 0;
+  static int per_sm[64];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 64) return cudaErrorInvalidDevice;
+  if (!((configured >> dev) & 1ull)) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::kSmem);
+    if (e != cudaSuccess) return e;
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, T::NT, T::kSmem);
+    if (e != cudaSuccess) return e;
+    per_sm[dev] = nb > 0 ? nb : 1;
+    configured |= 1ull << dev;
+  }
+  if (a.ntiles <= 0) return cudaSuccess;
+  const int slots = a.num_sms * per_sm[dev];
+  const int grid = a.ntiles < slots ? a.ntiles : slots;
+  kern<<<grid, T::NT, T::kSmem, st>>>(a.inst, a.table, a.ntiles, a.cur, a.status, a.sched);
+  return cudaGetLastError();
+}
+
+template <int N, int MODE>
+static cudaError_t launch_batch_nm(const BatchLaunch& a, cudaStream_t st) {
+  if (a.variant == 1) return launch_batch_nmr<N, MODE, 1>(a, st);
+  if constexpr (N <= 3) return launch_batch_nmr<N, MODE, 2>(a, st);
+  return cudaErrorInvalidValue;  // 16-row tiles do not fit for n >= 4
+}
+
+template <int N>
+static cudaError_t launch_batch_n(const BatchLaunch& a, cudaStream_t st) {
+  switch (a.mode) {
+    case kGeneral: return launch_batch_nm<N, kGeneral>(a, st);
+    case kTau1: return launch_batch_nm<N, kTau1>(a, st);
+    case kFast: return launch_batch_nm<N, kFast>(a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_batch_step(const BatchLaunch& a, cudaStream_t st) {
+  switch (a.n) {
+    case 1: return launch_batch_n<1>(a, st);
+    case 2: return launch_batch_n<2>(a, st);
+    case 3: return launch_batch_n<3>(a, st);
+    case 4: return launch_batch_n<4>(a, st);
+    case 5: return launch_batch_n<5>(a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <int N>
 static cudaError_t launch_n(const StepLaunch& a, cudaStream_t st) {
   const bool tau1 = (a.P.omega == 1.f);
   const bool w32 = (a.P.nw == 3 && a.P.mw == 2);
-  bool nn = true;  // spreading coefficients only between neighbouring interfaces
-  for (int l = 0; l < N; ++l)
-    for (int k = 2; k <= N - l; ++k) nn = nn && (a.P.S[l][k - 1] == 0.f);
   if (a.lattice == 2) {
-    if (!tau1) return launch_d2<N, kGeneral>(a, st);
-    if (w32 && nn) return launch_d2<N, kFast>(a, st);
-    return launch_d2<N, kTau1>(a, st);
+    switch (step_mode(a.P)) {
+      case kGeneral: return launch_d2<N, kGeneral>(a, st);
+      case kFast: return launch_d2<N, kFast>(a, st);
+      default: return launch_d2<N, kTau1>(a, st);
+    }
   }
   dim3 grid((a.P.nx + kD1TX - 1) / kD1TX);
   if (tau1) {

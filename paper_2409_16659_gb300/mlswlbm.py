@@ -21,6 +21,8 @@ MLSW_D1Q3 = 1
 MLSW_D2Q9 = 2
 MLSW_FLAG_SKIP_STABILITY_CHECK = 1
 MLSW_FLAG_NO_PERSISTENT = 2
+MLSW_BATCH_TILE8 = 1
+MLSW_BATCH_AUTOTUNE = 2
 
 MLSW_OK = 0
 MLSW_ERR_ARG = -1
@@ -89,6 +91,17 @@ EXPORTS = {
                                              ctypes.c_void_p, ctypes.c_void_p,
                                              ctypes.c_void_p, ctypes.c_void_p,
                                              ctypes.c_void_p]),
+    "mlswlbm_batch_create": (ctypes.c_int, [ctypes.c_int, _P, ctypes.POINTER(_F), ctypes.c_int,
+                                            ctypes.c_void_p, ctypes.POINTER(_H)]),
+    "mlswlbm_batch_step": (ctypes.c_int, [_H, ctypes.c_long]),
+    "mlswlbm_batch_get_heights": (ctypes.c_int, [_H, ctypes.c_int, _F]),
+    "mlswlbm_batch_modes": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_int), _D]),
+    "mlswlbm_batch_status": (ctypes.c_int, [_H]),
+    "mlswlbm_batch_tile_rows": (ctypes.c_int, [_H, ctypes.c_int]),
+    "mlswlbm_batch_launch_count": (ctypes.c_long, [_H]),
+    "mlswlbm_batch_groups": (ctypes.c_int, [_H]),
+    "mlswlbm_batch_destroy": (None, [_H]),
 }
 
 
@@ -379,3 +392,84 @@ def mlswlbm_diagnostics_noalloc(p, f, out, H=None, stream=None):
         _stream_ptr(stream if stream is not None else torch.cuda.current_stream()))
     _check(rc, "mlswlbm_diagnostics_noalloc")
     return out
+
+
+class Batch:
+    """Many independent D2Q9 lattices stepped together (mlswlbm_batch_*).
+
+    params: list of parameter dicts; heights: list of [n][ny][nx] arrays;
+    flags: MLSW_BATCH_TILE8 / MLSW_BATCH_AUTOTUNE; stream as for Solver.
+    """
+
+    def __init__(self, params, heights, flags=0, stream=None):
+        if len(params) != len(heights) or not params:
+            raise ValueError("need one heights array per parameter set")
+        self.count = len(params)
+        arr = (mlsw_params * self.count)()
+        self._h = []
+        for j, p in enumerate(params):
+            arr[j] = make_params(p)
+            n, ny, nx = int(p["n"]), int(p.get("ny", 1)), int(p.get("nx", 1))
+            self._h.append(_host_f32(heights[j], n * nx * ny))
+        self.shapes = [(int(p["n"]), int(p.get("ny", 1)), int(p.get("nx", 1))) for p in params]
+        ptrs = (_F * self.count)(*[_fptr(a) for a in self._h])
+        h = _H()
+        _check(lib().mlswlbm_batch_create(self.count, arr, ptrs, int(flags),
+                                          _stream_ptr(stream), ctypes.byref(h)),
+               "mlswlbm_batch_create")
+        self._b = h
+        self._h = None  # copied by the library
+
+    def step(self, nsteps=1):
+        _check(lib().mlswlbm_batch_step(self._b, int(nsteps)), "mlswlbm_batch_step")
+
+    def get_heights(self, index, out=None):
+        if out is None:
+            out = np.empty(self.shapes[index], dtype=np.float32)
+        rc = lib().mlswlbm_batch_get_heights(self._b, int(index),
+                                             _fptr(_checked_out(out, int(np.prod(self.shapes[index])))))
+        _check(rc, "mlswlbm_batch_get_heights")
+        return out
+
+    def modes(self, kx, ky):
+        """Complex hhat_i(q) of every layer (rows) of every instance: an array
+        [count][MLSW_MAX_LAYERS], zero beyond each instance's n."""
+        kx = np.ascontiguousarray(kx, dtype=np.int32)
+        ky = np.ascontiguousarray(ky, dtype=np.int32)
+        if kx.size != self.count or ky.size != self.count:
+            raise ValueError("one mode per instance")
+        out = np.zeros(2 * MLSW_MAX_LAYERS * self.count, dtype=np.float64)
+        ip = ctypes.POINTER(ctypes.c_int)
+        _check(lib().mlswlbm_batch_modes(self._b, kx.ctypes.data_as(ip), ky.ctypes.data_as(ip),
+                                         out.ctypes.data_as(_D)), "mlswlbm_batch_modes")
+        o = out.reshape(self.count, MLSW_MAX_LAYERS, 2)
+        return o[..., 0] + 1j * o[..., 1]
+
+    def status(self):
+        return lib().mlswlbm_batch_status(self._b)
+
+    def tile_rows(self, index):
+        return lib().mlswlbm_batch_tile_rows(self._b, int(index))
+
+    def launch_count(self):
+        return lib().mlswlbm_batch_launch_count(self._b)
+
+    def groups(self):
+        return lib().mlswlbm_batch_groups(self._b)
+
+    def close(self):
+        if getattr(self, "_b", None):
+            lib().mlswlbm_batch_destroy(self._b)
+            self._b = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
