@@ -25,7 +25,13 @@ Two more workloads are reported beside the main line, under "workloads"
     chip) and heights read back, wall clock;
   * three-layer lens field, D2Q9, 2048 x 2048, lenses of radius 200 (the
     droplet/lens equilibrium workload): LSU/s over event-timed
-    back-to-back steps; its 2 x 906 MB working set exceeds the L2.
+    back-to-back steps; its 2 x 906 MB working set exceeds the L2;
+  * batched stability sweep: 512 instances (2..5 layers, sides 64..512,
+    ~142 M layer-sites per step) in one batch with the tile-height
+    autotuner: LSU/s of the batched step, the time to solution of 2000
+    steps with the perturbed mode measured every 200 steps and a growth
+    rate fitted per instance, and the same steps run instance by instance
+    with one solver each (20 steps per instance, scaled to 2000).
 
 Reference arm (--impl reference): the FP64 CPU oracle on the host cores, one
 oracle step per benchmark step on a 128 x 128 patch with the same recipe.
@@ -377,7 +383,72 @@ def extra_workloads(B, torch):
             "roofline_frac": BYTES_PER_LSU * lsu / dt / 1e9 / peak,
             "l2": "back-to-back steps; 2 x 906 MB working set > 129 MB L2",
             "status": B.mlswlbm_strerror(s.status())}
+    out["stability_sweep_512"] = sweep_workload(B, torch)
     return out
+
+
+def sweep_workload(B, torch):
+    inst = workloads.sweep_instances()
+    params = [p for p, _, _, _ in inst]
+    heights = [h for _, h, _, _ in inst]
+    kx = [m[0] for _, _, m, _ in inst]
+    ky = [m[1] for _, _, m, _ in inst]
+    lsu = sum(p["n"] * p["nx"] * p["ny"] for p in params)
+    st = torch.cuda.current_stream()
+    res = {"instances": len(inst), "layer_sites_per_step": lsu}
+    t0 = time.perf_counter()
+    with B.Batch(params, heights, flags=B.MLSW_BATCH_AUTOTUNE, stream=st) as b:
+        torch.cuda.synchronize()
+        res["create_s"] = time.perf_counter() - t0
+        rows = [b.tile_rows(j) for j in range(len(inst))]
+        res["groups"] = b.groups()
+        res["tile_rows_16"] = rows.count(16)
+        res["tile_rows_8"] = rows.count(8)
+        b.step(3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        steps = 40
+        e0.record(st)
+        b.step(steps)
+        e1.record(st)
+        torch.cuda.synchronize()
+        dt = e0.elapsed_time(e1) * 1e-3 / steps
+        peak, _ = hbm_peak()
+        res.update({"value": lsu / dt, "unit": UNIT, "ms_per_step": 1e3 * dt,
+                    "roofline_frac": BYTES_PER_LSU * lsu / dt / 1e9 / peak})
+        # time to solution: 2000 steps, the perturbed mode every 200 steps,
+        # one growth rate per instance fitted to ln |hhat| of its top layer
+        t1 = time.perf_counter()
+        amp = [np.abs(b.modes(kx, ky))]
+        for _ in range(10):
+            b.step(200)
+            amp.append(np.abs(b.modes(kx, ky)))
+        amp = np.array(amp)  # [sample][instance][layer]
+        tt = 200.0 * np.arange(amp.shape[0])
+        rates = []
+        for j, p in enumerate(params):
+            a = amp[:, j, p["n"] - 1]
+            rates.append(float(np.polyfit(tt[5:], np.log(np.maximum(a[5:], 1e-300)), 1)[0]))
+        res["time_to_solution_s"] = time.perf_counter() - t1
+        res["growth_rate_range"] = [min(rates), max(rates)]
+        res["status"] = B.mlswlbm_strerror(b.status())
+    # the same work one solver per instance, one launch per step
+    t2 = time.perf_counter()
+    solvers = [B.Solver(p, h, stream=st) for p, h in zip(params, heights)]
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    per = 20
+    for s in solvers:
+        s.step(per)
+    torch.cuda.synchronize()
+    t4 = time.perf_counter()
+    for s in solvers:
+        s.close()
+    res["per_instance"] = {"create_s": t3 - t2, "ms_per_step": 1e3 * (t4 - t3) / per,
+                           "steps_timed": per, "note": "one Solver per instance, "
+                           "mlswlbm_step(20) each in turn, wall clock"}
+    res["speedup_vs_per_instance"] = res["per_instance"]["ms_per_step"] / res["ms_per_step"]
+    return res
 
 
 def run_profile(args):

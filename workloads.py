@@ -25,6 +25,16 @@ A contact angle theta is turned into the one-layer spreading coefficients by
 Young's law, cos(theta) = 1 + S_{i1} / gamma_{i+1,i+2}; multi-layer
 coefficients S_{ik}, k >= 2, are zero as in the paper's three-layer runs.
 
+Batched stability sweep (many uneven instances in one batch; the paper runs
+its linear-stability checks one film at a time):
+  * 512 instances, n uniform in 2..5, square sides from {64, 128, 256, 512},
+    tensions gamma_{i,i+1} log-uniform in [0.002, 0.02], viscosities
+    mu_1 = 1/16 and mu_i / mu_1 log-uniform in [0.25, 4], slip 1, (3, 2),
+    h* = 0.07, contact angle 20 degrees, layer means uniform in [0.6, 1.1];
+    every layer perturbed by 1e-4 a_i cos(2 pi (kx x + ky y) / side), a_i
+    uniform in [-1, 1] and (kx, ky) a random wavenumber with components in
+    0..8 (not both zero); seed 3.
+
 Droplet and lens equilibria (section "Droplet equilibria"; the paper gives
 no grid sizes, so these are stand-ins):
   * sessile ridge, D1Q3: one layer, precursor h*, a circular-arc ridge of
@@ -254,3 +264,33 @@ def lens3_heights(nx=128, ny=128, radius=12.5, theta0_deg=20.0, hstar=0.05, seed
         arc = np.maximum(arc, cap_profile(np.hypot(dx, dy), depth, 0.0, th))
     t2 = 0.3 * radius
     return np.stack([np.ones((ny, nx)), t2 - arc, hstar + 2.0 * arc])
+
+
+def sweep_instances(count=512, seed=3, sides=(64, 128, 256, 512), eps=1e-4):
+    """The batched stability sweep: a list of (params, heights [n][side][side]
+    float32, (kx, ky), amps) per instance."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        n = int(rng.integers(2, 6))
+        side = int(rng.choice(sides))
+        gamma = [float(g) for g in np.exp(rng.uniform(np.log(2e-3), np.log(2e-2), n))]
+        mu1 = 1.0 / 16.0
+        mu = [mu1] + [float(mu1 * r) for r in np.exp(rng.uniform(np.log(0.25), np.log(4.0), n - 1))]
+        p = dict(n=n, lattice=2, nx=side, ny=side, tau=1.0, gamma=gamma,
+                 S=_young_spreading(gamma, 20.0, n), mu=mu, beta=[1.0] * n, nw=3, mw=2,
+                 hstar=0.07)
+        means = rng.uniform(0.6, 1.1, n)
+        amps = rng.uniform(-1.0, 1.0, n)
+        while True:
+            kx, ky = (int(v) for v in rng.integers(0, 9, 2))
+            if kx or ky:
+                break
+        x = np.arange(side, dtype=np.float64)
+        ph = 2.0 * np.pi * (kx * x[None, :] + ky * x[:, None]) / side
+        mode = np.cos(ph)
+        h = np.empty((n, side, side), dtype=np.float32)
+        for i in range(n):
+            h[i] = means[i] + eps * amps[i] * mode
+        out.append((p, h, (kx, ky), amps))
+    return out
