@@ -451,6 +451,23 @@ def sweep_workload(B, torch):
     return res
 
 
+def run_profile_batch(args):
+    """Warm-up then --steps steps of the first 64 sweep instances (~1.4 GB)."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2409_16659_gb300 import mlswlbm as B
+    inst = workloads.sweep_instances()[:64]
+    with B.Batch([p for p, _, _, _ in inst], [h for _, h, _, _ in inst],
+                 stream=torch.cuda.current_stream()) as b:
+        b.step(args.warmup)
+        b.step(args.steps)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_batch_run": True, "groups": b.groups(),
+                          "launches": b.launch_count(),
+                          "status": B.mlswlbm_strerror(b.status())}), flush=True)
+    return 0
+
+
 def run_profile(args):
     """Warm-up then --steps back-to-back steps; no flush, e2e or CPU leg."""
     import torch
@@ -478,6 +495,8 @@ def main():
                     help="skip the D1Q3 film and 2048^2 lens workloads")
     ap.add_argument("--profile", action="store_true",
                     help="only warm-up + --steps back-to-back steps (for ncu captures)")
+    ap.add_argument("--profile-batch", action="store_true",
+                    help="the same for a 64-instance batch of the stability sweep")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -485,6 +504,8 @@ def main():
         return run_reference(args)
     if args.profile:
         return run_profile(args)
+    if args.profile_batch:
+        return run_profile_batch(args)
     return run_own(args)
 
 
