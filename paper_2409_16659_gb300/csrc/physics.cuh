@@ -327,22 +327,22 @@ __device__ __forceinline__ void friction(const KParams& P, const T (&h)[N], cons
           piv = r;
         }
       }
+      // the row exchange as selects on fixed indices, so that the system
+      // stays in registers
 #pragma unroll
       for (int r = c + 1; r < N; ++r) {
-        if (piv == r) {
+        const bool sw = (piv == r);
 #pragma unroll
-          for (int q = c; q < N; ++q) {
-            const float t = L[c][q];
-            L[c][q] = L[r][q];
-            L[r][q] = t;
-          }
-          float t = bx[c];
-          bx[c] = bx[r];
-          bx[r] = t;
-          t = by[c];
-          by[c] = by[r];
-          by[r] = t;
+        for (int q = c; q < N; ++q) {
+          const float a = L[c][q], b = L[r][q];
+          L[c][q] = sw ? b : a;
+          L[r][q] = sw ? a : b;
         }
+        const float ax = bx[c], bxr = bx[r], ay = by[c], byr = by[r];
+        bx[c] = sw ? bxr : ax;
+        bx[r] = sw ? ax : bxr;
+        by[c] = sw ? byr : ay;
+        by[r] = sw ? ay : byr;
       }
       inv_piv[c] = rcp(L[c][c]);
 #pragma unroll
