@@ -169,12 +169,29 @@ def dist_setup():
     return ws, rank, local
 
 
-def cpu_oracle_sample(seconds=12.0, side=256):
-    """The FP64 oracle on a bounded patch of the same workload recipe."""
-    import oracle
+def cpu_model():
+    """Host CPU description and core count, from /proc/cpuinfo."""
+    model, parts = None, set()
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                k, _, v = line.partition(":")
+                k, v = k.strip(), v.strip()
+                if k == "model name" and not model:
+                    model = v
+                elif k == "CPU part":
+                    parts.add(v)
+    except OSError:
+        pass
+    if not model and parts:
+        model = "Arm CPU part " + "/".join(sorted(parts))
+    return {"model": model or "unknown", "nproc": os.cpu_count()}
+
+
+def _oracle_lsu(oracle, side, seconds, threads):
+    oracle.set_threads(threads)
     p = workloads.film3_d2q9_params(side, side)
-    h0 = workloads.film3_d2q9_heights(side, side)
-    f = oracle.init(p, h0.ravel())
+    f = oracle.init(p, workloads.film3_d2q9_heights(side, side).ravel())
     steps, t0 = 0, time.perf_counter()
     while True:
         f = oracle.step(p, f)
@@ -182,10 +199,24 @@ def cpu_oracle_sample(seconds=12.0, side=256):
         if time.perf_counter() - t0 >= seconds:
             break
     dt = time.perf_counter() - t0
-    lsu = N_LAYERS * side * side * steps / dt
-    return {"value": lsu, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "FP64 C oracle, 1 thread, %d steps on a %dx%d patch of the 3-layer "
-                      "D2Q9 film (same parameters), %.1f s" % (steps, side, side, dt)}
+    return N_LAYERS * side * side * steps / dt, steps, dt
+
+
+def cpu_oracle_sample(seconds=8.0, side=256):
+    """The FP64 oracle on a bounded patch of the same workload recipe, on all
+    host cores (OpenMP over the cells) and on one thread."""
+    import oracle
+    cores = os.cpu_count() or 1
+    lsu, steps, dt = _oracle_lsu(oracle, side, seconds, cores)
+    lsu1, steps1, dt1 = _oracle_lsu(oracle, side, seconds, 1)
+    cpu = cpu_model()
+    return {"value": lsu, "unit": UNIT, "cores": cores,
+            "kind": "oracle",
+            "sample": "FP64 C oracle, %d OpenMP threads, %d steps on a %dx%d patch of the "
+                      "3-layer D2Q9 film (same parameters), %.1f s" % (cores, steps, side, side, dt),
+            "single_thread": {"value": lsu1, "unit": UNIT, "cores": 1,
+                              "sample": "same, 1 thread, %d steps, %.1f s" % (steps1, dt1)},
+            "cpu": cpu}
 
 
 def run_reference(args):
@@ -193,6 +224,8 @@ def run_reference(args):
     if rank != 0:
         return 0
     import oracle
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
     side = 128
     p = workloads.film3_d2q9_params(side, side)
     f = oracle.init(p, workloads.film3_d2q9_heights(side, side).ravel())
@@ -203,15 +236,15 @@ def run_reference(args):
         f = oracle.step(p, f)
     dt = time.perf_counter() - t0
     lsu = N_LAYERS * side * side * args.steps / dt
-    sample = ("FP64 C oracle, 1 thread, one oracle step per benchmark step on a %dx%d patch "
-              "of the 3-layer D2Q9 film (same parameters)" % (side, side))
+    sample = ("FP64 C oracle, %d OpenMP threads, one oracle step per benchmark step on a "
+              "%dx%d patch of the 3-layer D2Q9 film (same parameters)" % (cores, side, side))
     line = {"impl": "reference", "metric": METRIC, "value": lsu, "unit": UNIT,
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_dict({"sample_nx": side, "sample_ny": side}),
-            "cpu_baseline": {"value": lsu, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "cpu_baseline": {"value": lsu, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample, "cpu": cpu_model()},
             "e2e": {"value": lsu, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

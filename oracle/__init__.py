@@ -61,6 +61,8 @@ def lib():
             "orc_moments": (None, [P, _D, _D, _D, _D]),
             "orc_step": (ctypes.c_int, [P, _D, _D]),
             "orc_run": (ctypes.c_int, [P, _D, ctypes.c_long]),
+            "orc_set_threads": (None, [ctypes.c_int]),
+            "orc_max_threads": (ctypes.c_int, []),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -240,3 +242,12 @@ def run(p, f, nsteps):
 
 def heights(p, f):
     return moments(p, f)[0]
+
+
+def set_threads(n):
+    """Threads of the oracle's per-cell loops (results do not depend on it)."""
+    lib().orc_set_threads(int(n))
+
+
+def max_threads():
+    return int(lib().orc_max_threads())

@@ -316,6 +316,7 @@ void orc_moments(const orc_params* P, const double* f, double* h, double* Jx,
   int Q = orc_Q(P);
   long nc = (long)P->nx * P->ny;
   for (int i = 0; i < P->n; ++i)
+#pragma omp parallel for schedule(static)
     for (long c = 0; c < nc; ++c) {
       double s = 0.0, sx = 0.0, sy = 0.0;
       for (int k = 0; k < Q; ++k) {
@@ -362,7 +363,12 @@ int orc_step(const orc_params* P, const double* fin, double* fout) {
   /* 1. moments */
   orc_moments(P, fin, h, Jx, Jy);
 
+  /* Every cell of each stage below reads time-t fields and writes only its
+     own entries, so the cells are split across OpenMP threads; the
+     arithmetic and its order per cell do not depend on the thread count. */
+
   /* 2. interface heights z_i = sum_{j<=i} h_j */
+#pragma omp parallel for schedule(static)
   for (long c = 0; c < nc; ++c) {
     double acc = 0.0;
     for (int i = 0; i < n; ++i) {
@@ -373,6 +379,7 @@ int orc_step(const orc_params* P, const double* fin, double* fout) {
 
   /* 3. grad z, lap z (R5) */
   for (int i = 0; i < n; ++i)
+#pragma omp parallel for schedule(static)
     for (long y = 0; y < ny; ++y)
       for (long x = 0; x < nx; ++x) {
         long c = y * nx + x;
@@ -390,6 +397,7 @@ int orc_step(const orc_params* P, const double* fin, double* fout) {
       }
 
   /* 4. pressures */
+#pragma omp parallel for schedule(static)
   for (long c = 0; c < nc; ++c) {
     double hc[ORC_MAXN], gx[ORC_MAXN], gy[ORC_MAXN], lc[ORC_MAXN];
     double La[ORC_MAXN], Pc[ORC_MAXN], pc[ORC_MAXN];
@@ -403,7 +411,9 @@ int orc_step(const orc_params* P, const double* fin, double* fout) {
     for (int i = 0; i < n; ++i) p[i * nc + c] = pc[i];
   }
 
-  /* 5-9. grad p, friction, force, collision, streaming */
+  /* 5-9. grad p, friction, force, collision, streaming (each source cell
+     writes its own nine destinations) */
+#pragma omp parallel for schedule(static) reduction(min : status)
   for (long y = 0; y < ny; ++y)
     for (long x = 0; x < nx; ++x) {
       long c = y * nx + x;
@@ -460,3 +470,15 @@ int orc_run(const orc_params* P, double* f, long nsteps) {
   free(g);
   return status;
 }
+
+/* ------------------------------------------------------------------ */
+/* threads of the cell loops (OpenMP; 1 when built without it)         */
+/* ------------------------------------------------------------------ */
+#ifdef _OPENMP
+#include <omp.h>
+void orc_set_threads(int n) { omp_set_num_threads(n > 0 ? n : 1); }
+int orc_max_threads(void) { return omp_get_max_threads(); }
+#else
+void orc_set_threads(int n) { (void)n; }
+int orc_max_threads(void) { return 1; }
+#endif

@@ -91,6 +91,11 @@ int orc_step(const orc_params* P, const double* fin, double* fout);
 /* nsteps steps in place on f (uses an internal second buffer) */
 int orc_run(const orc_params* P, double* f, long nsteps);
 
+/* Threads of the per-cell loops (OpenMP): the results do not depend on
+   the count. orc_max_threads() is the count in use, 1 without OpenMP. */
+void orc_set_threads(int n);
+int orc_max_threads(void);
+
 #ifdef __cplusplus
 }
 #endif

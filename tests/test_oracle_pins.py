@@ -572,3 +572,16 @@ def test_free_energy_non_increasing_while_dewetting():
     assert np.all(np.diff(F) <= 1e-12 * abs(F[0]))
     assert F[-1] < 0.97 * F[0]
     assert h.min() < 0.06  # the film has ruptured down to the precursor
+
+
+def test_oracle_results_do_not_depend_on_thread_count():
+    # the per-cell loops run on OpenMP threads; every cell's arithmetic is
+    # the same whatever the split, so the state is bit-identical
+    p = workloads.film3_d2q9_params(48, 40)
+    f0 = oracle.init(p, workloads.film3_d2q9_heights(48, 40).ravel())
+    out, before = [], oracle.max_threads()
+    for t in (1, 3, max(before, 4)):
+        oracle.set_threads(t)
+        out.append(oracle.run(p, f0.copy(), 5))
+    oracle.set_threads(before)
+    assert all(np.array_equal(out[0], o) for o in out[1:])
