@@ -35,8 +35,9 @@
  *   - Inside a handle the rest population of layer i is stored shifted by a
  *     per-layer constant H_i (f_0 - H_i; H_i = median of the layer in
  *     h_init), which keeps the long-wave height differences and the small
- *     fluxes of precursor films representable in FP32. mlswlbm_get_state / mlswlbm_set_state convert to and from the
- *     true populations; mlswlbm_save_state / mlswlbm_load_state move the
+ *     fluxes of precursor films representable in FP32. mlswlbm_get_state /
+ *     mlswlbm_set_state convert to and from the true populations;
+ *     mlswlbm_save_state / mlswlbm_load_state move the
  *     internal representation unchanged (bit-exact checkpoints).
  */
 #ifndef MLSWLBM_H
@@ -182,6 +183,28 @@ int mlswlbm_load_state(mlsw_handle* h, const float* H_in, const float* g_in);
  */
 int mlswlbm_get_diagnostics(mlsw_handle* h, double* mass, double* kinetic,
                             double* hmin);
+
+/* Free energy of Eq. (free_energy_n_layer) in its long-wave form,
+ *   F = sum_x [ sum_{i=1..n} gamma_{i,i+1} (1 + |grad z_i|^2 / 2)
+ *             + sum_{i=0..n-1} sum_{k=1..n-i} S_ik phi_k(z_{i+k} - z_i)
+ *               (1 + |grad z_i|^2 / 2) ]     (z_0 = 0, flat substrate),
+ * with the lattice gradient of the step, summed on the device in FP64 from
+ * the current heights and the parameters of create (in double). A quantity
+ * the relaxation lowers (section Model); with the kinetic energy of
+ * mlswlbm_get_diagnostics it serves as the stop criterion of equilibrium
+ * runs. Synchronises; status as mlswlbm_get_heights. */
+int mlswlbm_get_free_energy(mlsw_handle* h, double* F);
+
+/* Steps until the kinetic energy sum_{i,x} |J_i|^2 / (2 h_i) (as in
+ * mlswlbm_get_diagnostics) is below ke_threshold, checked after every
+ * check_every >= 1 steps (a run starting from rest has none, so at least
+ * min(check_every, max_steps) steps are taken), or until max_steps >= 0
+ * steps are done. *steps_done and *kinetic (either may be NULL) receive the
+ * steps taken and the last kinetic energy; the caller compares it with the
+ * threshold to see which limit ended the run. Synchronises at every check;
+ * errors as mlswlbm_step and mlswlbm_get_diagnostics. */
+int mlswlbm_step_until(mlsw_handle* h, long max_steps, long check_every, double ke_threshold,
+                       long* steps_done, double* kinetic);
 
 /* Synchronises and returns MLSW_OK or MLSW_ERR_NONFINITE (a kernel saw
  * h <= 0 or a non-finite value since create or the last call); clears it. */

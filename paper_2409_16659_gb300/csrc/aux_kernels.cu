@@ -504,3 +504,95 @@ cudaError_t launch_batch_heights(const BatchInst* inst_host, int cur, float* h, 
 }
 
 }  // namespace mlsw
+
+namespace mlsw {
+
+// ---------------------------------------------------------------------------
+// free energy, Eq. (free_energy_n_layer) in the long-wave form,
+//   F = sum_x [ sum_{i=1..n} gamma_i (1 + |grad z_i|^2 / 2)
+//             + sum_{i=0..n-1} sum_{k=1..n-i} S_ik phi_k(z_{i+k} - z_i)
+//               (1 + |grad z_i|^2 / 2) ],  z_0 = 0,
+// with the lattice gradient of the step (isotropic stencil), from dense
+// heights [n][ny][nx], in FP64. Two passes: per-block partial sums, then
+// their sum in a fixed order.
+// ---------------------------------------------------------------------------
+constexpr int kFreeThreads = 256;
+
+__device__ __forceinline__ double phi_d(const FreeEnergyParams& E, int k, double h) {
+  const double r = k * E.hstar / h;
+  return (E.nw * pow(r, (double)E.mw) - E.mw * pow(r, (double)E.nw)) / (double)(E.nw - E.mw);
+}
+
+__global__ void __launch_bounds__(kFreeThreads)
+    free_energy_partial_kernel(FreeEnergyParams E, const float* __restrict__ h,
+                               double* __restrict__ partials) {
+  __shared__ double red[kFreeThreads / 32];
+  const int n = E.n, nx = E.nx, ny = E.ny;
+  const long ncell = (long)nx * ny;
+  double acc = 0.0;
+  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < ncell;
+       c += (long)gridDim.x * blockDim.x) {
+    const int y = (int)(c / nx), x = (int)(c - (long)y * nx);
+    const int xe = x + 1 == nx ? 0 : x + 1, xw = x == 0 ? nx - 1 : x - 1;
+    const int yn = y + 1 == ny ? 0 : y + 1, ys = y == 0 ? ny - 1 : y - 1;
+    double z[kMaxLayers + 1], g2[kMaxLayers + 1];
+    z[0] = 0.0;
+    g2[0] = 0.0;
+    double zE = 0, zW = 0, zN = 0, zS = 0, zNE = 0, zNW = 0, zSE = 0, zSW = 0;
+    for (int i = 1; i <= n; ++i) {
+      const float* hi = h + (long)(i - 1) * ncell;
+      z[i] = z[i - 1] + (double)hi[(long)y * nx + x];
+      zE += hi[(long)y * nx + xe];
+      zW += hi[(long)y * nx + xw];
+      double gx, gy;
+      if (E.lattice == 2) {
+        zN += hi[(long)yn * nx + x];
+        zS += hi[(long)ys * nx + x];
+        zNE += hi[(long)yn * nx + xe];
+        zNW += hi[(long)yn * nx + xw];
+        zSE += hi[(long)ys * nx + xe];
+        zSW += hi[(long)ys * nx + xw];
+        // (1/cs^2) sum_k w_k c_k z(x + c_k): 1/3 on the axes, 1/12 on the diagonals
+        gx = (zE - zW) / 3.0 + ((zNE - zNW) + (zSE - zSW)) / 12.0;
+        gy = (zN - zS) / 3.0 + ((zNE - zSE) + (zNW - zSW)) / 12.0;
+      } else {
+        gx = 0.5 * (zE - zW);
+        gy = 0.0;
+      }
+      g2[i] = gx * gx + gy * gy;
+      acc += E.gamma[i - 1] * (1.0 + 0.5 * g2[i]);
+    }
+    for (int i = 0; i < n; ++i)
+      for (int k = 1; k <= n - i; ++k)
+        acc += E.S[i][k - 1] * phi_d(E, k, z[i + k] - z[i]) * (1.0 + 0.5 * g2[i]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < kFreeThreads / 32; ++w) s += red[w];
+    partials[blockIdx.x] = s;
+  }
+}
+
+__global__ void free_energy_final_kernel(int nblk, const double* __restrict__ partials,
+                                         double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += partials[b];
+    *out = s;
+  }
+}
+
+cudaError_t launch_free_energy(const FreeEnergyParams& E, const float* h, double* partials,
+                               int nblk, double* out, cudaStream_t st) {
+  free_energy_partial_kernel<<<nblk, kFreeThreads, 0, st>>>(E, h, partials);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  free_energy_final_kernel<<<1, 32, 0, st>>>(nblk, partials, out);
+  return cudaGetLastError();
+}
+
+}  // namespace mlsw

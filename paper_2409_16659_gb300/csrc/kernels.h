@@ -121,6 +121,18 @@ cudaError_t launch_diagnostics(int lattice, int n, const Layout& L, const float*
                                const KShift& sh, double* partials, int nblk, double* out,
                                cudaStream_t st);
 
+// Free energy of Eq. (free_energy_n_layer) from dense heights [n][ny][nx],
+// FP64, with the parameters in double precision. partials: nblk doubles.
+struct FreeEnergyParams {
+  int n, lattice, nx, ny;
+  double gamma[kMaxLayers];
+  double S[kMaxLayers][kMaxLayers];
+  double hstar;
+  int nw, mw;
+};
+cudaError_t launch_free_energy(const FreeEnergyParams& E, const float* h, double* partials,
+                               int nblk, double* out, cudaStream_t st);
+
 // Friction of independent cells (layout [i][cell]); Jy / Ry may be null.
 cudaError_t launch_friction_eval(const KParams& P, long ncell, const float* h, const float* Jx,
                                  const float* Jy, float* Rx, float* Ry, cudaStream_t st);

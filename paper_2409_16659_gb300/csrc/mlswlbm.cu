@@ -634,6 +634,50 @@ int mlswlbm_get_diagnostics(mlsw_handle* h, double* mass, double* kinetic, doubl
   return mlswlbm_status(h);
 }
 
+int mlswlbm_get_free_energy(mlsw_handle* h, double* F) {
+  if (!h || !F) return MLSW_ERR_ARG;
+  const mlsw_params& p = h->p;
+  mlsw::FreeEnergyParams E;
+  std::memset(&E, 0, sizeof(E));
+  E.n = p.n_layers;
+  E.lattice = p.lattice;
+  E.nx = p.nx;
+  E.ny = p.ny;
+  for (int i = 0; i < p.n_layers; ++i) {
+    E.gamma[i] = p.gamma[i];
+    for (int k = 1; k <= p.n_layers - i; ++k) E.S[i][k - 1] = p.spread[i][k - 1];
+  }
+  E.hstar = p.hstar;
+  E.nw = p.wet_n;
+  E.mw = p.wet_m;
+  CU(mlsw::launch_heights(h->Q, p.n_layers, h->kp.L, h->f[h->cur], h->sh, h->hbuf, h->stream));
+  CU(mlsw::launch_free_energy(E, h->hbuf, h->partials, h->nblk_diag, h->dout, h->stream));
+  h->launches += 3;
+  CU(cudaMemcpyAsync(F, h->dout, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  return mlswlbm_status(h);
+}
+
+int mlswlbm_step_until(mlsw_handle* h, long max_steps, long check_every, double ke_threshold,
+                       long* steps_done, double* kinetic) {
+  if (!h || max_steps < 0 || check_every < 1) return MLSW_ERR_ARG;
+  // a run starts from rest (zero kinetic energy), so the criterion is only
+  // tested after steps have been taken
+  long done = 0;
+  double ke = 0.0;
+  int rc = MLSW_OK;
+  while (done < max_steps) {
+    const long chunk = std::min(check_every, max_steps - done);
+    rc = mlswlbm_step(h, chunk);
+    if (rc != MLSW_OK) break;
+    done += chunk;
+    rc = mlswlbm_get_diagnostics(h, nullptr, &ke, nullptr);
+    if (rc != MLSW_OK || ke < ke_threshold) break;
+  }
+  if (steps_done) *steps_done = done;
+  if (kinetic) *kinetic = ke;
+  return rc;
+}
+
 int mlswlbm_set_stream(mlsw_handle* h, void* stream) {
   if (!h) return MLSW_ERR_ARG;
   h->stream = (cudaStream_t)stream;

@@ -81,6 +81,9 @@ EXPORTS = {
     "mlswlbm_load_state": (ctypes.c_int, [_H, _F, _F]),
     "mlswlbm_get_diagnostics": (ctypes.c_int, [_H, _D, _D, _D]),
     "mlswlbm_status": (ctypes.c_int, [_H]),
+    "mlswlbm_get_free_energy": (ctypes.c_int, [_H, _D]),
+    "mlswlbm_step_until": (ctypes.c_int, [_H, ctypes.c_long, ctypes.c_long, ctypes.c_double,
+                                          ctypes.POINTER(ctypes.c_long), _D]),
     "mlswlbm_set_stream": (ctypes.c_int, [_H, ctypes.c_void_p]),
     "mlswlbm_launch_count": (ctypes.c_long, [_H]),
     "mlswlbm_destroy": (None, [_H]),
@@ -259,6 +262,20 @@ class Solver:
     def set_heights(self, h):
         a = _host_f32(h, self.n * self.ncell)
         _check(lib().mlswlbm_set_heights(self._h, _fptr(a)), "mlswlbm_set_heights")
+
+    def free_energy(self):
+        F = ctypes.c_double()
+        _check(lib().mlswlbm_get_free_energy(self._h, ctypes.byref(F)), "mlswlbm_get_free_energy")
+        return F.value
+
+    def step_until(self, max_steps, check_every, ke_threshold):
+        """Steps until the kinetic energy drops below ke_threshold; returns
+        (steps taken, last kinetic energy)."""
+        done, ke = ctypes.c_long(), ctypes.c_double()
+        _check(lib().mlswlbm_step_until(self._h, int(max_steps), int(check_every),
+                                        float(ke_threshold), ctypes.byref(done), ctypes.byref(ke)),
+               "mlswlbm_step_until")
+        return done.value, ke.value
 
     def get_state(self, out=None):
         shape = (self.n, self.Q, self.ny, self.nx)

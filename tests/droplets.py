@@ -146,3 +146,40 @@ def lens3_angles(h, centres, radius):
         lo = fit_angle_radial(p2[-3:].mean() - z2, cc, rmax, 0.0)
         out.append((up, lo))
     return out
+
+
+def free_energy(p, h):
+    """Free energy of Eq. (free_energy_n_layer), long-wave form, from heights
+    [n][ny][nx] with the lattice gradient of the step (isotropic stencil on
+    D2Q9, central difference on D1Q3); S_ik phi_k for the wetting terms."""
+    n = int(p["n"])
+    h = np.asarray(h, dtype=np.float64).reshape(n, int(p["ny"]), int(p["nx"]))
+    z = np.concatenate([np.zeros((1,) + h.shape[1:]), np.cumsum(h, axis=0)])
+
+    def sh(a, dx, dy):  # a(x + dx, y + dy), periodic
+        return np.roll(np.roll(a, -dx, axis=-1), -dy, axis=-2)
+
+    def grad2(a):
+        if int(p["lattice"]) == 2:
+            gx = (sh(a, 1, 0) - sh(a, -1, 0)) / 3.0 + ((sh(a, 1, 1) - sh(a, -1, 1))
+                                                      + (sh(a, 1, -1) - sh(a, -1, -1))) / 12.0
+            gy = (sh(a, 0, 1) - sh(a, 0, -1)) / 3.0 + ((sh(a, 1, 1) - sh(a, 1, -1))
+                                                      + (sh(a, -1, 1) - sh(a, -1, -1))) / 12.0
+            return gx * gx + gy * gy
+        gx = 0.5 * (sh(a, 1, 0) - sh(a, -1, 0))
+        return gx * gx
+
+    g2 = [np.zeros(h.shape[1:])] + [grad2(z[i]) for i in range(1, n + 1)]
+    hs, nw, mw = float(p["hstar"]), int(p["nw"]), int(p["mw"])
+
+    def phi(k, t):
+        r = k * hs / t
+        return (nw * r ** mw - mw * r ** nw) / (nw - mw)
+
+    F = 0.0
+    for i in range(1, n + 1):
+        F += (p["gamma"][i - 1] * (1.0 + 0.5 * g2[i])).sum()
+    for i in range(0, n):
+        for k in range(1, n - i + 1):
+            F += (p["S"][i][k - 1] * phi(k, z[i + k] - z[i]) * (1.0 + 0.5 * g2[i])).sum()
+    return float(F)

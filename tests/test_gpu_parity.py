@@ -375,3 +375,53 @@ def test_three_layer_lens_field_128_matches_oracle_angles():
     # drifts by ~1e-5 (a 1e-9 bias per step from FP32 rounding of the
     # rest population), the flat layers by < 1e-6
     np.testing.assert_allclose(h.sum(axis=(1, 2)), gold["mass"], rtol=5e-5)
+
+
+# --------------------------------------------------------------------------
+# free energy (Eq. free_energy_n_layer) and the kinetic-energy stop
+# criterion of equilibrium runs
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("lat", [1, 2])
+def test_free_energy_matches_the_formula_on_read_back_heights(lat):
+    if lat == 2:
+        p = workloads.random_params(41, 3, B.MLSW_D2Q9, 72, 40, multilayer_S=True)
+    else:
+        p = workloads.random_params(42, 4, B.MLSW_D1Q3, 300, 1, multilayer_S=True)
+    with B.Solver(p, workloads.random_heights(43, p)) as s:
+        s.step(50)
+        F = s.free_energy()
+        want = droplets.free_energy(p, s.get_heights().astype(np.float64))
+    assert F == pytest.approx(want, rel=1e-10, abs=1e-12)
+
+
+def test_free_energy_decreases_while_a_film_dewets():
+    g, th = 0.01, np.radians(30)
+    S = g * (np.cos(th) - 1)
+    p = dict(n=2, lattice=1, nx=128, ny=1, tau=1.0, gamma=[g, g], S=[[S, 0.0], [S]],
+             mu=[1 / 6, 1 / 6], beta=[1.0, 1.0], nw=3, mw=2, hstar=0.05)
+    rng = np.random.default_rng(7)
+    h0 = (0.25 + 1e-3 * rng.uniform(-1, 1, (2, 1, 128)))
+    with B.Solver(p, h0) as s:
+        F = []
+        for _ in range(25):
+            F.append(s.free_energy())
+            s.step(1000)
+        hmin = s.get_heights().min()
+    assert np.all(np.diff(F) <= 1e-9 * abs(F[0]))
+    assert F[-1] < 0.97 * F[0] and hmin < 0.06
+
+
+def test_step_until_stops_on_kinetic_energy():
+    p = workloads.lens3_params(128, 128, 12.5)
+    h0 = workloads.lens3_heights(128, 128, 12.5)
+    with B.Solver(p, h0) as s:
+        done, ke = s.step_until(200000, 500, 2e-6)
+        assert ke < 2e-6 and 0 < done < 200000 and done % 500 == 0
+        _, ke2, _ = s.get_diagnostics()
+        assert ke2 == ke
+        # a threshold met at the first check: one chunk is taken
+        done2, _ = s.step_until(1000, 100, 1.0)
+        assert done2 == 100
+        # a threshold out of reach: stops at max_steps
+        done3, ke3 = s.step_until(700, 300, 0.0)
+        assert done3 == 700 and ke3 > 0.0
