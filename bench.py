@@ -169,6 +169,22 @@ def dist_setup():
     return ws, rank, local
 
 
+def max_over_ranks(values, device):
+    """Each value's maximum over the ranks of the default process group (the
+    job's time is its slowest rank's); unchanged in a single process."""
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if torch.distributed.is_available() and torch.distributed.is_initialized():
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def job_rate(world_size, units_per_rank, seconds):
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (every rank runs its own lattice, weak scaling)."""
+    return world_size * units_per_rank / seconds
+
+
 def cpu_model():
     """Host CPU description and core count, from /proc/cpuinfo."""
     model, parts = None, set()
@@ -333,13 +349,10 @@ def run_own(args):
     status = solver.status()
     solver.close()
 
-    tot = torch.tensor([total_s, steady_s, e2e_s], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        torch.distributed.all_reduce(tot, op=torch.distributed.ReduceOp.MAX)
-    total_s, steady_s, e2e_s = [float(v) for v in tot.cpu()]
+    total_s, steady_s, e2e_s = max_over_ranks([total_s, steady_s, e2e_s], "cuda")
 
     if rank == 0:
-        value = ws * lsu_step * args.steps / total_s
+        value = job_rate(ws, lsu_step * args.steps, total_s)
         avg_launch_s = total_s / args.steps
         bytes_alg = BYTES_PER_LSU * lsu_step
         peak, peak_src = hbm_peak()
@@ -355,13 +368,13 @@ def run_own(args):
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "step_d2q9_tma<3,kFast>",
                          "bytes_per_launch_algorithmic": bytes_alg, "peak_source": peak_src},
-            "e2e": {"value": ws * lsu_step * k_e2e / e2e_s, "unit": UNIT,
+            "e2e": {"value": job_rate(ws, lsu_step * k_e2e, e2e_s), "unit": UNIT,
                     "h2d_bytes_per_step": int(h_host.numel() * 4),
                     "d2h_bytes_per_step": int(h_out.numel() * 4), "steps": k_e2e,
                     "api": "mlswlbm_set_heights + mlswlbm_step(1) + mlswlbm_get_heights"},
             "gpu_launches": int(launches),
             "clocks": clocks,
-            "steady_state": {"value": ws * lsu_step * args.steps / steady_s,
+            "steady_state": {"value": job_rate(ws, lsu_step * args.steps, steady_s),
                              "ms_per_step": 1e3 * steady_s / args.steps,
                              "note": "back-to-back steps without L2 flush"},
             "step_ms_p50": float(np.median(step_ms)), "step_ms_min": float(step_ms.min()),
