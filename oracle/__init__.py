@@ -7,7 +7,8 @@ TEST INFRASTRUCTURE ONLY. This package checks the CUDA path; only the tests,
 Parameters are plain dicts (the same data the CUDA binding receives):
     n, lattice (1 = D1Q3, 2 = D2Q9), nx, ny, tau,
     gamma[n]  (gamma_{i,i+1}), S[i][k-1] (S_{ik}, i = 0..n-1, k = 1..n-i),
-    mu[n], beta[n], nw, mw, hstar.
+    mu[n], beta[n], nw, mw, hstar, and optionally a sinusoidal substrate
+    sub_amp, sub_kx, sub_ky (z_0 = sub_amp cos 2 pi (kx x / nx + ky y / ny)).
 Arrays are float64 numpy arrays in the layouts documented in oracle.h.
 """
 import ctypes
@@ -35,6 +36,9 @@ class orc_params(ctypes.Structure):
         ("nw", ctypes.c_int),
         ("mw", ctypes.c_int),
         ("hstar", ctypes.c_double),
+        ("sub_amp", ctypes.c_double),
+        ("sub_kx", ctypes.c_int),
+        ("sub_ky", ctypes.c_int),
     ]
 
 
@@ -55,6 +59,8 @@ def lib():
             "orc_build_D": (None, [P, _D, _D]),
             "orc_friction": (ctypes.c_int, [P, _D, _D, _D, _D, _D]),
             "orc_pressures": (None, [P, _D, _D, _D, _D, _D, _D, _D]),
+            "orc_pressures_sub": (None, [P, _D, _D, _D, _D, ctypes.c_double, _D, _D, _D]),
+            "orc_substrate": (ctypes.c_double, [P, ctypes.c_long, ctypes.c_long]),
             "orc_equilibrium": (None, [P, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_double, _D]),
             "orc_init": (None, [P, _D, _D]),
@@ -94,6 +100,9 @@ def make_params(p: dict) -> orc_params:
     s.nw = int(p["nw"])
     s.mw = int(p["mw"])
     s.hstar = float(p["hstar"])
+    s.sub_amp = float(p.get("sub_amp", 0.0))
+    s.sub_kx = int(p.get("sub_kx", 0))
+    s.sub_ky = int(p.get("sub_ky", 0))
     return s
 
 
@@ -174,6 +183,23 @@ def friction(p, h, Jx, Jy=None):
     if rc != 0:
         raise FloatingPointError("singular boundary-condition matrix")
     return Rx, Ry
+
+
+def pressures_sub(p, h, gzx, gzy, lz, g0sq):
+    s = make_params(p)
+    n = s.n
+    args = [_vec(a, n) for a in (h, gzx, gzy, lz)]
+    La, Pi, pp = np.zeros(n), np.zeros(n), np.zeros(n)
+    lib().orc_pressures_sub(ctypes.byref(s), *[_ptr(a) for a in args], float(g0sq), _ptr(La),
+                            _ptr(Pi), _ptr(pp))
+    return La, Pi, pp
+
+
+def substrate(p):
+    """z_0 on the lattice, [ny][nx]."""
+    s = make_params(p)
+    return np.array([[lib().orc_substrate(ctypes.byref(s), x, y) for x in range(s.nx)]
+                     for y in range(s.ny)])
 
 
 def pressures(p, h, gzx, gzy, lz):

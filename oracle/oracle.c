@@ -247,10 +247,17 @@ int orc_friction(const orc_params* P, const double* h, const double* Jx,
 void orc_pressures(const orc_params* P, const double* h, const double* gzx,
                    const double* gzy, const double* lz, double* Lambda,
                    double* Pi, double* p) {
+  orc_pressures_sub(P, h, gzx, gzy, lz, 0.0, Lambda, Pi, p); /* flat (R9) */
+}
+
+void orc_pressures_sub(const orc_params* P, const double* h, const double* gzx,
+                       const double* gzy, const double* lz, double g0sq,
+                       double* Lambda, double* Pi, double* p) {
   int n = P->n;
+  /* z relative to the substrate: only thicknesses z_m - z_l enter below */
   double z[ORC_MAXN + 1], g2[ORC_MAXN + 1];
   z[0] = 0.0;
-  g2[0] = 0.0; /* grad z_0 = 0 (R9) */
+  g2[0] = g0sq; /* |grad z_0|^2 of the substrate */
   for (int i = 1; i <= n; ++i) {
     z[i] = z[i - 1] + h[i - 1];
     double gx = gzx[i - 1], gy = gzy ? gzy[i - 1] : 0.0;
@@ -331,6 +338,17 @@ void orc_moments(const orc_params* P, const double* f, double* h, double* Jx,
     }
 }
 
+static const double ORC_PI = 3.14159265358979323846;
+
+double orc_substrate(const orc_params* P, long x, long y) {
+  if (P->sub_amp == 0.0) return 0.0;
+  /* phase / (2 pi) = kx x / nx + ky y / ny, reduced exactly in integers */
+  long nx = P->nx, ny = P->ny, nc = nx * ny;
+  long m = (((long)P->sub_kx * x) % nx * ny + ((long)P->sub_ky * y) % ny * nx) % nc;
+  if (m < 0) m += nc;
+  return P->sub_amp * cos(2.0 * ORC_PI * (double)m / (double)nc);
+}
+
 static long wrap(long a, long m) {
   long r = a % m;
   return r < 0 ? r + m : r;
@@ -354,8 +372,11 @@ int orc_step(const orc_params* P, const double* fin, double* fout) {
   double* gzy = malloc(sizeof(double) * n * nc);
   double* lz = malloc(sizeof(double) * n * nc);
   double* p = malloc(sizeof(double) * n * nc);
-  if (!h || !Jx || !Jy || !z || !gzx || !gzy || !lz || !p) {
+  double* z0 = malloc(sizeof(double) * nc);
+  double* g0 = malloc(sizeof(double) * nc);
+  if (!h || !Jx || !Jy || !z || !gzx || !gzy || !lz || !p || !z0 || !g0) {
     free(h); free(Jx); free(Jy); free(z); free(gzx); free(gzy); free(lz); free(p);
+    free(z0); free(g0);
     return -1;
   }
   int status = 0;
@@ -367,10 +388,24 @@ int orc_step(const orc_params* P, const double* fin, double* fout) {
      own entries, so the cells are split across OpenMP threads; the
      arithmetic and its order per cell do not depend on the thread count. */
 
-  /* 2. interface heights z_i = sum_{j<=i} h_j */
+  /* 2. substrate z_0 with its squared lattice gradient (R5), interface
+     heights z_i = z_0 + sum_{j<=i} h_j */
+#pragma omp parallel for schedule(static)
+  for (long c = 0; c < nc; ++c) z0[c] = orc_substrate(P, c % nx, c / nx);
 #pragma omp parallel for schedule(static)
   for (long c = 0; c < nc; ++c) {
-    double acc = 0.0;
+    long x = c % nx, y = c / nx;
+    double sx = 0.0, sy = 0.0;
+    for (int k = 1; k < Q; ++k) {
+      long nb = wrap(y + cy[k], ny) * nx + wrap(x + cx[k], nx);
+      sx += w[k] * cx[k] * (z0[nb] - z0[c]);
+      sy += w[k] * cy[k] * (z0[nb] - z0[c]);
+    }
+    g0[c] = (sx / CS2) * (sx / CS2) + (sy / CS2) * (sy / CS2);
+  }
+#pragma omp parallel for schedule(static)
+  for (long c = 0; c < nc; ++c) {
+    double acc = z0[c];
     for (int i = 0; i < n; ++i) {
       acc += h[i * nc + c];
       z[i * nc + c] = acc;
@@ -407,7 +442,7 @@ int orc_step(const orc_params* P, const double* fin, double* fout) {
       gy[i] = gzy[i * nc + c];
       lc[i] = lz[i * nc + c];
     }
-    orc_pressures(P, hc, gx, gy, lc, La, Pc, pc);
+    orc_pressures_sub(P, hc, gx, gy, lc, g0[c], La, Pc, pc);
     for (int i = 0; i < n; ++i) p[i * nc + c] = pc[i];
   }
 
@@ -455,6 +490,7 @@ int orc_step(const orc_params* P, const double* fin, double* fout) {
     }
 
   free(h); free(Jx); free(Jy); free(z); free(gzx); free(gzy); free(lz); free(p);
+  free(z0); free(g0);
   return status;
 }
 

@@ -44,6 +44,10 @@ typedef struct {
   double beta[ORC_MAXN];         /* beta[i-1] = beta_i                      */
   int nw, mw;                    /* wetting exponents, nw > mw              */
   double hstar;                  /* precursor thickness h*                  */
+  /* substrate z_0(x, y) = sub_amp cos(2 pi (sub_kx x / nx + sub_ky y / ny));
+     sub_amp = 0 is the flat substrate of the paper's runs */
+  double sub_amp;
+  int sub_kx, sub_ky;
 } orc_params;
 
 /* wetting potential phi_k(h) and its derivative, Eq. (wetting_potential) */
@@ -57,6 +61,9 @@ void orc_spreading_from_tensions(orc_params* P, const double* g);
 /* lattice tables */
 int orc_Q(const orc_params* P);
 void orc_lattice(const orc_params* P, int* cx, int* cy, double* w);
+
+/* substrate height z_0 at cell (x, y) */
+double orc_substrate(const orc_params* P, long x, long y);
 
 /* the 3n x 3n boundary-condition matrix D at one cell (row-major) */
 void orc_build_D(const orc_params* P, const double* h, double* D);
@@ -73,6 +80,12 @@ int orc_friction(const orc_params* P, const double* h, const double* Jx,
 void orc_pressures(const orc_params* P, const double* h, const double* gzx,
                    const double* gzy, const double* lz, double* Lambda,
                    double* Pi, double* p);
+
+/* the same on a corrugated substrate: g0sq = |grad z_0|^2 at the cell
+ * (orc_pressures is this with g0sq = 0) */
+void orc_pressures_sub(const orc_params* P, const double* h, const double* gzx,
+                       const double* gzy, const double* lz, double g0sq,
+                       double* Lambda, double* Pi, double* p);
 
 /* equilibrium populations of one layer at one cell, Eq. (equilibrium_distribution) */
 void orc_equilibrium(const orc_params* P, double h, double Ux, double Uy,

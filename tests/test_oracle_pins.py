@@ -585,3 +585,75 @@ def test_oracle_results_do_not_depend_on_thread_count():
         out.append(oracle.run(p, f0.copy(), 5))
     oracle.set_threads(before)
     assert all(np.array_equal(out[0], o) for o in out[1:])
+
+
+# --------------------------------------------------------------------------
+# corrugated substrate z_0(x) (section Model: z_0 is the substrate height;
+# Eq. disjoining_pressure carries (1 + |grad z_0|^2 / 2) on its substrate
+# terms); here z_0 = A cos(2 pi (kx x / nx + ky y / ny))
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("seed", range(4))
+def test_pressures_on_a_corrugated_substrate_explicit(seed):
+    p, h, gzx, gzy, lz = _rand_pressure_case(2, seed)
+    g0 = np.random.default_rng(100 + seed).uniform(0.0, 0.3)
+    La, Pi, pr = oracle.pressures_sub(p, h, gzx, gzy, lz, g0)
+    S = p["S"]
+    z1, z2 = h[0], h[0] + h[1]
+    g1 = gzx[0] ** 2 + gzy[0] ** 2
+    phi = lambda i, k, d: S[i][k - 1] * lsa.phi_k(p, k, d)
+    dphi = lambda i, k, d: S[i][k - 1] * lsa.dphi_k(p, k, d)
+    # the substrate's terms carry (1 + |grad z_0|^2 / 2)
+    d1 = (dphi(0, 1, z1) * (1 + g0 / 2) - dphi(1, 1, z2 - z1) * (1 + g1 / 2)
+          - (p["gamma"][0] + phi(1, 1, z2 - z1)) * lz[0])
+    d2 = (dphi(1, 1, z2 - z1) * (1 + g1 / 2) + dphi(0, 2, z2) * (1 + g0 / 2)
+          - p["gamma"][1] * lz[1])
+    assert pr[1] == pytest.approx(d2, rel=1e-12, abs=1e-16)
+    assert pr[0] == pytest.approx(d1 + d2, rel=1e-12, abs=1e-16)
+    # g0 = 0 is the flat substrate
+    assert np.array_equal(oracle.pressures_sub(p, h, gzx, gzy, lz, 0.0)[2],
+                          oracle.pressures(p, h, gzx, gzy, lz)[2])
+
+
+@pytest.mark.parametrize("lat", [1, 2])
+def test_zero_amplitude_substrate_is_the_flat_one(lat):
+    p = workloads.random_params(51, 2, lat, 24, 1 if lat == 1 else 16)
+    h = workloads.random_heights(52, p)
+    q = dict(p, sub_amp=0.0, sub_kx=3, sub_ky=1)
+    a = oracle.run(p, oracle.init(p, h.ravel()), 20)
+    b = oracle.run(q, oracle.init(q, h.ravel()), 20)
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("lat,n", [(1, 1), (1, 2), (2, 1), (2, 2)])
+def test_flat_surface_over_a_corrugated_substrate_is_steady(lat, n):
+    # without wetting terms (S = 0) the pressure is the Laplace pressure of
+    # the interfaces: films that fill a corrugated substrate up to a flat
+    # free surface carry none, so nothing moves
+    nx, ny = (48, 1) if lat == 1 else (24, 16)
+    p = _p(n=n, lattice=lat, nx=nx, ny=ny, sub_amp=0.05, sub_kx=2, sub_ky=0 if lat == 1 else 1)
+    z0 = oracle.substrate(p)
+    h = np.stack([0.8 - z0] + [np.full_like(z0, 0.5)] * (n - 1))
+    out = oracle.heights(p, oracle.run(p, oracle.init(p, h.ravel()), 500)).reshape(h.shape)
+    assert np.abs(out - h).max() < 1e-12
+
+
+@pytest.mark.parametrize("lat", [1, 2])
+def test_film_on_a_sinusoidal_substrate_takes_the_linear_response(lat):
+    # linearising p = -gamma lap z_1 + S phi'(z_1 - z_0) = const about a film
+    # of thickness h0 gives the surface modulation
+    #   eps = A S phi''(h0) / (gamma q^2 + S phi''(h0))
+    # with q^2 minus the lattice Laplacian's symbol; started from a flat
+    # surface, the film relaxes to it
+    nx, ny, mode, steps = (64, 1, (4, 0), 30000) if lat == 1 else (32, 32, (2, 1), 10000)
+    A, g, S, h0 = 2e-3, 0.01, 0.002, 0.5
+    p = _p(n=1, lattice=lat, nx=nx, ny=ny, gamma=[g], S=[[S]], sub_amp=A, sub_kx=mode[0],
+           sub_ky=mode[1])
+    z0 = oracle.substrate(p)
+    f = oracle.run(p, oracle.init(p, (h0 - z0).ravel()), steps)
+    z1 = z0 + oracle.heights(p, f).reshape(ny, nx)
+    eps = (np.fft.fft2(z1)[mode[1] % ny, mode[0] % nx] * 2 / (nx * ny)).real
+    q2 = -lsa.symbols(p, (2 * np.pi * mode[0] / nx, 2 * np.pi * mode[1] / ny))[2].real
+    sp = S * lsa.ddphi_k(p, 1, h0)
+    want = A * sp / (g * q2 + sp)
+    assert 0.5 * A < want < 0.8 * A  # the pin separates following from ignoring the substrate
+    assert eps == pytest.approx(want, rel=1e-3)
