@@ -96,6 +96,14 @@ typedef struct mlsw_params {
   int wet_n, wet_m;
   double hstar;
   int flags; /* MLSW_FLAG_* */
+  /* substrate height z_0(x, y) = sub_amp cos(2 pi (sub_kx x / nx + sub_ky y / ny))
+   * (section Model: z_0 is the possibly corrugated substrate); sub_amp = 0
+   * is the flat substrate of the paper's runs. It enters the interface
+   * heights z_i = z_0 + sum_{j<=i} h_j, hence every Laplace and slope term,
+   * and the factor (1 + |grad z_0|^2 / 2) of the substrate's terms in
+   * Eq. (disjoining_pressure). D1Q3 needs sub_ky = 0. */
+  double sub_amp;
+  int sub_kx, sub_ky;
 } mlsw_params;
 
 typedef struct mlsw_handle mlsw_handle;

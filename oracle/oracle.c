@@ -36,7 +36,9 @@
  *       forcing term, w_k c_k . F_i / c_s^2. No velocity shift.
  *   R8  D2Q9 velocities are the integer vectors; sqrt(2) in the printed list is
  *       the length of the diagonal ones.
- *   R9  the substrate is flat: z_0 = 0 and grad z_0 = 0.
+ *   R9  the substrate is flat (z_0 = 0) unless a sinusoidal z_0 is given
+ *       (sub_amp, sub_kx, sub_ky); z_0 enters the interface heights and the
+ *       (1 + |grad z_0|^2 / 2) factor of the substrate's wetting terms.
  */
 #include "oracle.h"
 
@@ -132,7 +134,7 @@ void orc_build_D(const orc_params* P, const double* h, double* D) {
   for (int i = 1; i <= n; ++i) z[i] = z[i - 1] + h[i - 1];
   for (int r = 0; r < N3 * N3; ++r) D[r] = 0.0;
 #define DD(r, c) D[(r) * N3 + (c)]
-  /* Eq. (no_slip) at the substrate, z_0 = 0 (R1, R9) */
+  /* Eq. (no_slip) at the substrate, heights measured from z_0 (R1, R9) */
   double b1 = P->beta[0];
   double zb = z[0] - b1;
   DD(0, 0) = zb * zb;

@@ -511,7 +511,7 @@ namespace mlsw {
 // free energy, Eq. (free_energy_n_layer) in the long-wave form,
 //   F = sum_x [ sum_{i=1..n} gamma_i (1 + |grad z_i|^2 / 2)
 //             + sum_{i=0..n-1} sum_{k=1..n-i} S_ik phi_k(z_{i+k} - z_i)
-//               (1 + |grad z_i|^2 / 2) ],  z_0 = 0,
+//               (1 + |grad z_i|^2 / 2) ],  z_0 the substrate,
 // with the lattice gradient of the step (isotropic stencil), from dense
 // heights [n][ny][nx], in FP64. Two passes: per-block partial sums, then
 // their sum in a fixed order.
@@ -536,9 +536,30 @@ __global__ void __launch_bounds__(kFreeThreads)
     const int xe = x + 1 == nx ? 0 : x + 1, xw = x == 0 ? nx - 1 : x - 1;
     const int yn = y + 1 == ny ? 0 : y + 1, ys = y == 0 ? ny - 1 : y - 1;
     double z[kMaxLayers + 1], g2[kMaxLayers + 1];
-    z[0] = 0.0;
-    g2[0] = 0.0;
-    double zE = 0, zW = 0, zN = 0, zS = 0, zNE = 0, zNW = 0, zSE = 0, zSW = 0;
+    // the substrate z_0 at the cell and its neighbours, its squared gradient
+    auto z0 = [&](int xx, int yy) {
+      if (E.sub_amp == 0.0) return 0.0;
+      long m = ((long)E.sub_kx * xx % nx) * ny + ((long)E.sub_ky * yy % ny) * nx;
+      m %= ncell;
+      if (m < 0) m += ncell;
+      return E.sub_amp * cospi(2.0 * (double)m / (double)ncell);
+    };
+    z[0] = z0(x, y);
+    double zE = z0(xe, y), zW = z0(xw, y), zN = 0, zS = 0, zNE = 0, zNW = 0, zSE = 0, zSW = 0;
+    if (E.lattice == 2) {
+      zN = z0(x, yn);
+      zS = z0(x, ys);
+      zNE = z0(xe, yn);
+      zNW = z0(xw, yn);
+      zSE = z0(xe, ys);
+      zSW = z0(xw, ys);
+      const double gx = (zE - zW) / 3.0 + ((zNE - zNW) + (zSE - zSW)) / 12.0;
+      const double gy = (zN - zS) / 3.0 + ((zNE - zSE) + (zNW - zSW)) / 12.0;
+      g2[0] = gx * gx + gy * gy;
+    } else {
+      const double gx = 0.5 * (zE - zW);
+      g2[0] = gx * gx;
+    }
     for (int i = 1; i <= n; ++i) {
       const float* hi = h + (long)(i - 1) * ncell;
       z[i] = z[i - 1] + (double)hi[(long)y * nx + x];

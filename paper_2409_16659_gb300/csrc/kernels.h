@@ -129,6 +129,8 @@ struct FreeEnergyParams {
   double S[kMaxLayers][kMaxLayers];
   double hstar;
   int nw, mw;
+  double sub_amp;  // substrate z_0 = sub_amp cos(2 pi (kx x / nx + ky y / ny))
+  int sub_kx, sub_ky;
 };
 cudaError_t launch_free_energy(const FreeEnergyParams& E, const float* h, double* partials,
                                int nblk, double* out, cudaStream_t st);

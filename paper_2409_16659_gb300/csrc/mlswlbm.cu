@@ -135,6 +135,9 @@ KParams make_kparams(const mlsw_params& p) {
   k.mw = p.wet_m;
   k.c_phi = (float)(1.0 / (p.wet_n - p.wet_m));
   k.c_dphi = (float)((double)p.wet_n * p.wet_m / (p.wet_n - p.wet_m));
+  k.sub_amp = (float)p.sub_amp;
+  k.sub_kx = p.sub_kx;
+  k.sub_ky = p.sub_ky;
   return k;
 }
 
@@ -380,6 +383,8 @@ int mlswlbm_check_params(const mlsw_params* p) {
   if (!std::isfinite(p->tau) || !(p->tau > 0.5)) return MLSW_ERR_ARG;
   if (!finite_pos(p->hstar)) return MLSW_ERR_ARG;
   if (p->wet_m < 1 || p->wet_n <= p->wet_m || p->wet_n > 64) return MLSW_ERR_ARG;
+  if (!std::isfinite(p->sub_amp)) return MLSW_ERR_ARG;
+  if (p->sub_amp != 0.0 && p->lattice == MLSW_D1Q3 && p->sub_ky != 0) return MLSW_ERR_ARG;
   for (int i = 0; i < n; ++i) {
     if (!finite_pos(p->mu[i])) return MLSW_ERR_ARG;
     if (!std::isfinite(p->beta[i]) || p->beta[i] < 0.0) return MLSW_ERR_ARG;
@@ -650,6 +655,9 @@ int mlswlbm_get_free_energy(mlsw_handle* h, double* F) {
   E.hstar = p.hstar;
   E.nw = p.wet_n;
   E.mw = p.wet_m;
+  E.sub_amp = p.sub_amp;
+  E.sub_kx = p.sub_kx;
+  E.sub_ky = p.sub_ky;
   CU(mlsw::launch_heights(h->Q, p.n_layers, h->kp.L, h->f[h->cur], h->sh, h->hbuf, h->stream));
   CU(mlsw::launch_free_energy(E, h->hbuf, h->partials, h->nblk_diag, h->dout, h->stream));
   h->launches += 3;

@@ -63,7 +63,23 @@ struct KParams {
   // 1 when a side of the lattice is shorter than 4 cells: a real column or
   // row can then have several ghost images
   int tiny;
+  // substrate z_0(x, y) = sub_amp cos(2 pi (sub_kx x / nx + sub_ky y / ny));
+  // sub_amp = 0 is the flat substrate
+  float sub_amp;
+  int sub_kx, sub_ky;
 };
+
+// Substrate height at lattice cell (x, y) (any integers: the cosine is
+// periodic); the phase is reduced exactly in integers.
+__device__ __forceinline__ float substrate_at(const KParams& P, int x, int y) {
+  const long nx = P.nx, ny = P.ny, nc = nx * ny;
+  long m = ((long)P.sub_kx * x % nx) * ny + ((long)P.sub_ky * y % ny) * nx;
+  m %= nc;
+  if (m < 0) m += nc;
+  float s, c;
+  sincospif(2.f * (float)((double)m / (double)nc), &s, &c);
+  return P.sub_amp * c;
+}
 
 // ---------------------------------------------------------------------------
 // lattices (section LBM): c_0 = 0, then the paper's order
@@ -162,8 +178,8 @@ __device__ __forceinline__ void wet_powers(const KParams& P, T r, T& rm, T& rn) 
 // Every interface pair (l, m = l + k), 0 <= l < m <= N, enters once with
 // the thickness d = z_m - z_l between them: E = S_lk phi'_k(d)
 // (1 + |grad z_l|^2 / 2) is subtracted from Pi_l and added to Pi_m, and
-// S_lk phi_k(d) raises the tension of interface l. l = 0 is the flat
-// substrate (grad z_0 = 0, no pressure of its own).
+// S_lk phi_k(d) raises the tension of interface l. l = 0 is the substrate
+// (height z0, slope factor sg0; no pressure of its own).
 // The inputs are the deviations of the interface heights, zd[i - 1] =
 // z_i - (H_1 + ... + H_i), so d = Hsum[l][m] + (zd_m - zd_l) (zd_0 = 0): the
 // deviations are O(1e-3) numbers and their differences carry the FP32
@@ -172,10 +188,14 @@ __device__ __forceinline__ void wet_powers(const KParams& P, T r, T& rm, T& rn) 
 // NN: only nearest-neighbour pairs (k = 1) carry a spreading coefficient
 // (S_{lk} = 0 for k >= 2, as in the paper's three-layer runs); the pair loop
 // is then branch-free.
+// z0, sg0: the substrate height z_0 (on the scale of zd) and 1 + |grad z_0|^2 / 2
+// at the cell; 0 and 1 for the flat substrate.
 template <int N, bool W32, class T, bool NN = false>
 __device__ __forceinline__ void layer_pressures_dev(const KParams& P, const T (&zd)[N],
                                                     const T (&gx)[N], const T (&gy)[N],
-                                                    const T (&lz)[N], T (&p)[N]) {
+                                                    const T (&lz)[N], T (&p)[N],
+                                                    T z0 = Num<T>::splat(0.f),
+                                                    T sg0 = Num<T>::splat(1.f)) {
   T ten[N], pi[N], sg[N];
 #pragma unroll
   for (int i = 0; i < N; ++i) {
@@ -185,8 +205,8 @@ __device__ __forceinline__ void layer_pressures_dev(const KParams& P, const T (&
   }
 #pragma unroll
   for (int l = 0; l < N; ++l) {
-    const T sgl = (l == 0) ? Num<T>::splat(1.f) : sg[l > 0 ? l - 1 : 0];
-    const T zl = (l == 0) ? Num<T>::splat(0.f) : zd[l > 0 ? l - 1 : 0];
+    const T sgl = (l == 0) ? sg0 : sg[l > 0 ? l - 1 : 0];
+    const T zl = (l == 0) ? z0 : zd[l > 0 ? l - 1 : 0];
 #pragma unroll
     for (int m = l + 1; m <= (NN ? l + 1 : N); ++m) {
       const int k = m - l;

@@ -137,6 +137,7 @@ template <> struct Lanes<float> {
   __device__ static float ld(const float* a, const float*) { return *a; }
   __device__ static void st(float* a, float*, float v) { *a = v; }
   __device__ static float get(float v, int) { return v; }
+  __device__ static float ld2(float a, float) { return a; }
 };
 template <> struct Lanes<f2> {
   static constexpr int W = 2;
@@ -146,6 +147,7 @@ template <> struct Lanes<f2> {
     *b = v.v.y;
   }
   __device__ static float get(f2 v, int l) { return l ? v.v.y : v.v.x; }
+  __device__ static f2 ld2(float a, float b) { return mk2(a, b); }
 };
 
 // ---------------------------------------------------------------------------
@@ -297,6 +299,10 @@ __device__ __forceinline__ void d2q9_tile_loop(const Tiles& tiles, int* __restri
     const long lplane = (long)Q * L.plane;  // floats per layer
     float* __restrict__ fout = tr.fout;
     const int x0 = tr.bx * TX, y0 = tr.by * TY;
+    // a corrugated substrate (never in the fast mode): z starts at z_0
+    const bool sub = MODE != kFast && P.sub_amp != 0.f;
+    // z_0 at tile-local cell (c, r) of the two-ring region (c, r from -2)
+    auto z0_at = [&](int c, int r) { return substrate_at(P, x0 + c, y0 + r); };
 
     // ---- M. moments: deviations z on the two-ring region, J on the tile ----
     {
@@ -304,6 +310,7 @@ __device__ __forceinline__ void d2q9_tile_loop(const Tiles& tiles, int* __restri
       const float* sA = stage + rA * BW + (c + 2);  // stage column = c + 2
       const float* sB = stage + rB * BW + (c + 2);
       T z = Num<T>::splat(0.f);
+      if (sub) z = Ln::ld2(z0_at(ix, rA - 2), z0_at(ix, rB - 2));
 #pragma unroll
       for (int i = 0; i < N; ++i) {
         T v[Q];
@@ -325,6 +332,7 @@ __device__ __forceinline__ void d2q9_tile_loop(const Tiles& tiles, int* __restri
       halo_cell(tid, r, c);
       const float* src = stage + r * BW + (c + 2);
       T z = Num<T>::splat(0.f);
+      if (sub) z = Num<T>::splat(z0_at(c - 2, r - 2));
 #pragma unroll
       for (int i = 0; i < N; ++i) {
         T v[Q];
@@ -375,7 +383,32 @@ __device__ __forceinline__ void d2q9_tile_loop(const Tiles& tiles, int* __restri
           lz[i] = fmav((zE + zW) + (zN + zS), 2.f / 3.f,
                        fmav((zNE + zNW) + (zSE + zSW), 1.f / 6.f, zd[i] * (-10.f / 3.f)));
         }
-        layer_pressures_dev<N, W32, U, NN>(P, zd, gzx, gzy, lz, p);
+        if (sub) {
+          // z_0 and 1 + |grad z_0|^2 / 2 (lattice stencil) at the two cells;
+          // p-region cell (pr, pc) is tile cell (pc - 1, pr - 1)
+          U z0c, sg0;
+          {
+            float zc[2], sg[2];
+            const int ca[2] = {pcA - 1, pcB - 1}, ra[2] = {prA - 1, prB - 1};
+#pragma unroll
+            for (int l = 0; l < 2; ++l) {
+              const float c0 = z0_at(ca[l], ra[l]);
+              const float e = z0_at(ca[l] + 1, ra[l]), w = z0_at(ca[l] - 1, ra[l]);
+              const float nn = z0_at(ca[l], ra[l] + 1), ss = z0_at(ca[l], ra[l] - 1);
+              const float ne = z0_at(ca[l] + 1, ra[l] + 1), nw = z0_at(ca[l] - 1, ra[l] + 1);
+              const float se = z0_at(ca[l] + 1, ra[l] - 1), sw = z0_at(ca[l] - 1, ra[l] - 1);
+              const float gx = fmaf(e - w, 1.f / 3.f, ((ne - nw) + (se - sw)) * (1.f / 12.f));
+              const float gy = fmaf(nn - ss, 1.f / 3.f, ((ne - se) + (nw - sw)) * (1.f / 12.f));
+              zc[l] = c0;
+              sg[l] = fmaf(0.5f, fmaf(gx, gx, gy * gy), 1.f);
+            }
+            z0c = LU::ld2(zc[0], zc[1]);
+            sg0 = LU::ld2(sg[0], sg[1]);
+          }
+          layer_pressures_dev<N, W32, U, NN>(P, zd, gzx, gzy, lz, p, z0c, sg0);
+        } else {
+          layer_pressures_dev<N, W32, U, NN>(P, zd, gzx, gzy, lz, p);
+        }
 #pragma unroll
         for (int i = 0; i < N; ++i)
           LU::st(ps + (i * PH + prA) * PW + pcA, ps + (i * PH + prB) * PW + pcB, p[i]);
@@ -405,6 +438,7 @@ __device__ __forceinline__ void d2q9_tile_loop(const Tiles& tiles, int* __restri
         T hh[N], dd[N], jx[N], jy[N];
         {
           T zprev = Num<T>::splat(0.f);
+          if (sub) zprev = Ln::ld2(z0_at(ix, iyA), z0_at(ix, iyB));
 #pragma unroll
           for (int i = 0; i < N; ++i) {
             const T zi = Ln::ld(zs + (i * RH + iyA + 2) * RW + ix + 2,
@@ -550,10 +584,12 @@ __global__ void __launch_bounds__(256, 2)
 // both give the same bits.
 // ---------------------------------------------------------------------------
 // p_i of one cell from z deviations at x - 1, x, x + 1
+// z0w, z0c, z0e: the substrate at x - 1, x, x + 1 (all 0 when flat)
 template <int N, bool W32>
 __device__ __forceinline__ void d1q3_pressures(const KParams& P, const float (&zw)[N],
                                                const float (&zc)[N], const float (&ze)[N],
-                                               float (&p)[N]) {
+                                               float (&p)[N], float z0w = 0.f, float z0c = 0.f,
+                                               float z0e = 0.f) {
   float zd[N], gxz[N], gyz[N], lz[N];
 #pragma unroll
   for (int i = 0; i < N; ++i) {
@@ -563,7 +599,12 @@ __device__ __forceinline__ void d1q3_pressures(const KParams& P, const float (&z
     gyz[i] = 0.f;
     lz[i] = e + wv;            // (2/cs^2) w_1 = 1
   }
-  layer_pressures_dev<N, W32>(P, zd, gxz, gyz, lz, p);
+  if (P.sub_amp != 0.f) {
+    const float g0 = 0.5f * (z0e - z0w);
+    layer_pressures_dev<N, W32>(P, zd, gxz, gyz, lz, p, z0c, fmaf(0.5f, g0 * g0, 1.f));
+  } else {
+    layer_pressures_dev<N, W32>(P, zd, gxz, gyz, lz, p);
+  }
 }
 
 // Force, collision with forcing, for one cell: fs[i][k] receives the
@@ -607,9 +648,10 @@ __global__ void __launch_bounds__(TX)
   const int nx = P.nx;
   const int x0 = blockIdx.x * TX, tx = threadIdx.x;
 
+  const bool sub = P.sub_amp != 0.f;
   float hh[N], dd[N], jx[N];
   {
-    float z = 0.f;
+    float z = sub ? substrate_at(P, x0 + tx, 0) : 0.f;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
       const float f0 = __ldg(fin + L.at(i * Q + 0, x0 + tx, 0));
@@ -626,7 +668,7 @@ __global__ void __launch_bounds__(TX)
   if (tx < 4) {
     const int rc = tx < 2 ? tx : RW - 4 + tx;  // columns x0 - 2, x0 - 1, x0 + TX, x0 + TX + 1
     const int x = x0 - 2 + rc;
-    float z = 0.f;
+    float z = sub ? substrate_at(P, x, 0) : 0.f;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
       const float f0 = __ldg(fin + L.at(i * Q + 0, x, 0));
@@ -646,7 +688,13 @@ __global__ void __launch_bounds__(TX)
       zc[i] = zs[i][rc];
       ze[i] = zs[i][rc + 1];
     }
-    d1q3_pressures<N, W32>(P, zw, zc, ze, p);
+    if (sub) {
+      const int x = x0 - 1 + pc;
+      d1q3_pressures<N, W32>(P, zw, zc, ze, p, substrate_at(P, x - 1, 0), substrate_at(P, x, 0),
+                             substrate_at(P, x + 1, 0));
+    } else {
+      d1q3_pressures<N, W32>(P, zw, zc, ze, p);
+    }
 #pragma unroll
     for (int i = 0; i < N; ++i) ps[i][pc] = p[i];
   }
@@ -714,7 +762,7 @@ __global__ void __launch_bounds__(kD1PT)
   for (int s = 0; s < nsteps; ++s) {
     // moments -> z
     for (int x = tid; x < nx; x += kD1PT) {
-      float z = 0.f;
+      float z = P.sub_amp != 0.f ? substrate_at(P, x, 0) : 0.f;
 #pragma unroll
       for (int i = 0; i < N; ++i) {
         z += fa[(i * Q + 0) * nx + x] + (fa[(i * Q + 1) * nx + x] + fa[(i * Q + 2) * nx + x]);
@@ -732,7 +780,11 @@ __global__ void __launch_bounds__(kD1PT)
         zc[i] = zsm[i * nx + x];
         ze[i] = zsm[i * nx + xe];
       }
-      d1q3_pressures<N, W32>(P, zw, zc, ze, p);
+      if (P.sub_amp != 0.f)
+        d1q3_pressures<N, W32>(P, zw, zc, ze, p, substrate_at(P, x - 1, 0),
+                               substrate_at(P, x, 0), substrate_at(P, x + 1, 0));
+      else
+        d1q3_pressures<N, W32>(P, zw, zc, ze, p);
 #pragma unroll
       for (int i = 0; i < N; ++i) psm[i * nx + x] = p[i];
     }
@@ -817,7 +869,7 @@ int step_mode(const KParams& P) {
   bool nn = true;  // spreading coefficients only between neighbouring interfaces
   for (int l = 0; l < P.n; ++l)
     for (int k = 2; k <= P.n - l; ++k) nn = nn && (P.S[l][k - 1] == 0.f);
-  return (w32 && nn) ? kFast : kTau1;
+  return (w32 && nn && P.sub_amp == 0.f) ? kFast : kTau1;
 }
 
 // batch kernels: dynamic shared memory and occupancy, once per device and

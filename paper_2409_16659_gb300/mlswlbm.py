@@ -52,6 +52,9 @@ class mlsw_params(ctypes.Structure):
         ("wet_m", ctypes.c_int),
         ("hstar", ctypes.c_double),
         ("flags", ctypes.c_int),
+        ("sub_amp", ctypes.c_double),
+        ("sub_kx", ctypes.c_int),
+        ("sub_ky", ctypes.c_int),
     ]
 
 
@@ -157,6 +160,9 @@ def make_params(p):
     s.wet_m = int(p["mw"])
     s.hstar = float(p["hstar"])
     s.flags = int(p.get("flags", 0))
+    s.sub_amp = float(p.get("sub_amp", 0.0))
+    s.sub_kx = int(p.get("sub_kx", 0))
+    s.sub_ky = int(p.get("sub_ky", 0))
     return s
 
 

@@ -151,10 +151,15 @@ def lens3_angles(h, centres, radius):
 def free_energy(p, h):
     """Free energy of Eq. (free_energy_n_layer), long-wave form, from heights
     [n][ny][nx] with the lattice gradient of the step (isotropic stencil on
-    D2Q9, central difference on D1Q3); S_ik phi_k for the wetting terms."""
+    D2Q9, central difference on D1Q3); S_ik phi_k for the wetting terms; the
+    substrate z_0 of the parameters (sinusoidal, or flat)."""
     n = int(p["n"])
-    h = np.asarray(h, dtype=np.float64).reshape(n, int(p["ny"]), int(p["nx"]))
-    z = np.concatenate([np.zeros((1,) + h.shape[1:]), np.cumsum(h, axis=0)])
+    ny, nx = int(p["ny"]), int(p["nx"])
+    h = np.asarray(h, dtype=np.float64).reshape(n, ny, nx)
+    y, x = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    z0 = float(p.get("sub_amp", 0.0)) * np.cos(
+        2 * np.pi * (int(p.get("sub_kx", 0)) * x / nx + int(p.get("sub_ky", 0)) * y / ny))
+    z = np.concatenate([z0[None], z0[None] + np.cumsum(h, axis=0)])
 
     def sh(a, dx, dy):  # a(x + dx, y + dy), periodic
         return np.roll(np.roll(a, -dx, axis=-1), -dy, axis=-2)
@@ -169,7 +174,7 @@ def free_energy(p, h):
         gx = 0.5 * (sh(a, 1, 0) - sh(a, -1, 0))
         return gx * gx
 
-    g2 = [np.zeros(h.shape[1:])] + [grad2(z[i]) for i in range(1, n + 1)]
+    g2 = [grad2(z[i]) for i in range(0, n + 1)]
     hs, nw, mw = float(p["hstar"]), int(p["nw"]), int(p["mw"])
 
     def phi(k, t):

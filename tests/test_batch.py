@@ -29,6 +29,9 @@ def _mixed_instances():
                                  (15, 1, 96, 32, 1.0), (16, 2, 33, 17, 1.0)]:
         p = workloads.random_params(seed, n, B.MLSW_D2Q9, nx, ny, tau=tau)
         out.append((p, workloads.random_heights(100 + seed, p)))
+    # on a corrugated substrate
+    p = dict(workloads.random_params(17, 3, B.MLSW_D2Q9, 48, 32), sub_amp=0.1, sub_kx=2, sub_ky=1)
+    out.append((p, workloads.random_heights(117, p)))
     return out
 
 

@@ -425,3 +425,63 @@ def test_step_until_stops_on_kinetic_energy():
         # a threshold out of reach: stops at max_steps
         done3, ke3 = s.step_until(700, 300, 0.0)
         assert done3 == 700 and ke3 > 0.0
+
+
+# --------------------------------------------------------------------------
+# corrugated substrate z_0 = A cos(2 pi (kx x / nx + ky y / ny))
+# --------------------------------------------------------------------------
+SUB_ONE_STEP = [(n, lat, tau) for n in (1, 2, 3, 5) for lat, tau in ((2, 1.0), (2, 0.8), (1, 1.0))]
+
+
+@pytest.mark.parametrize("n,lat,tau", SUB_ONE_STEP)
+def test_one_step_on_a_corrugated_substrate(n, lat, tau):
+    p, f = one_step_case(n, lat, tau)
+    p = dict(p, sub_amp=0.2, sub_kx=3, sub_ky=0 if lat == 1 else 2)
+    hmax = oracle.heights(p, f).max()
+    with B.Solver(p, oracle.heights(p, f)) as s:
+        s.set_state(f)
+        s.step(1)
+        fg = s.get_state().astype(np.float64)
+        assert s.status() == B.MLSW_OK
+    fr = oracle.step(p, f)
+    assert np.abs(fg - fr).max() <= 4e-6 * hmax
+
+
+@pytest.mark.parametrize("lat", [1, 2])
+def test_film_on_a_corrugated_substrate_multistep(lat):
+    if lat == 2:
+        p = dict(workloads.random_params(61, 2, 2, 45, 33), sub_amp=0.05, sub_kx=2, sub_ky=1)
+        steps = 300
+    else:  # the persistent one-CTA kernel
+        p = dict(workloads.random_params(62, 2, 1, 128, 1), sub_amp=0.05, sub_kx=3, sub_ky=0)
+        steps = 1000
+    h0 = workloads.random_heights(63, p, 0.5, 1.1, 2e-3)
+    hg, hr = _run_both(p, h0, steps)
+    assert _relmax(hg, hr) <= 1e-5
+
+
+def test_substrate_translation_by_one_period_is_bit_exact():
+    # z_0 with kx = 4 on 64 columns and ky = 2 on 40 rows repeats after 16
+    # columns and 20 rows; shifting the film by that moves every cell to a
+    # new tile position over the same substrate height
+    p = dict(workloads.random_params(64, 3, 2, 64, 40), sub_amp=0.1, sub_kx=4, sub_ky=2)
+    h0 = workloads.random_heights(65, p, 0.5, 1.1, 1e-2).astype(np.float32)
+    hs = np.roll(np.roll(h0, 16, axis=2), 20, axis=1)
+    with B.Solver(p, h0) as a, B.Solver(p, hs) as b:
+        a.step(40)
+        b.step(40)
+        ha, hb = a.get_heights(), b.get_heights()
+    assert np.array_equal(np.roll(np.roll(ha, 16, axis=2), 20, axis=1), hb)
+
+
+@pytest.mark.parametrize("lat", [1, 2])
+def test_free_energy_on_a_corrugated_substrate(lat):
+    if lat == 2:
+        p = dict(workloads.random_params(66, 2, 2, 40, 24), sub_amp=0.1, sub_kx=1, sub_ky=2)
+    else:
+        p = dict(workloads.random_params(67, 3, 1, 200, 1), sub_amp=0.1, sub_kx=2, sub_ky=0)
+    with B.Solver(p, workloads.random_heights(68, p)) as s:
+        s.step(30)
+        F = s.free_energy()
+        want = droplets.free_energy(p, s.get_heights().astype(np.float64))
+    assert F == pytest.approx(want, rel=1e-10, abs=1e-12)
