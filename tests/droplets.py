@@ -188,3 +188,29 @@ def free_energy(p, h):
         for k in range(1, n - i + 1):
             F += (p["S"][i][k - 1] * phi(k, z[i + k] - z[i]) * (1.0 + 0.5 * g2[i])).sum()
     return float(F)
+
+
+def radial_spectrum(field, nbins=None):
+    """Azimuthally averaged power |hhat(q)|^2 of a periodic 2-D field
+    (mean removed), in unit-width bins of |k| (integer wavenumbers)."""
+    f = np.asarray(field, dtype=np.float64)
+    ny, nx = f.shape
+    P = np.abs(np.fft.fft2(f - f.mean())) ** 2
+    ky = np.fft.fftfreq(ny) * ny
+    kx = np.fft.fftfreq(nx) * nx
+    k = np.hypot(kx[None, :], ky[:, None])
+    b = np.rint(k).astype(int)
+    nb = nbins or min(nx, ny) // 2
+    s = np.bincount(b.ravel(), weights=P.ravel(), minlength=nb + 1)[:nb]
+    c = np.bincount(b.ravel(), minlength=nb + 1)[:nb]
+    return s / np.maximum(c, 1)
+
+
+def rupture_step(sample, hstar, every, limit):
+    """First multiple of `every` (up to `limit`) at which some layer of
+    sample(t) -> heights falls below 1.5 h*, with the heights then."""
+    for t in range(every, limit + 1, every):
+        h = sample(t)
+        if h.min() < 1.5 * hstar:
+            return t, h
+    return None, None

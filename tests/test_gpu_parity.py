@@ -485,3 +485,45 @@ def test_free_energy_on_a_corrugated_substrate(lat):
         F = s.free_energy()
         want = droplets.free_energy(p, s.get_heights().astype(np.float64))
     assert F == pytest.approx(want, rel=1e-10, abs=1e-12)
+
+
+# --------------------------------------------------------------------------
+# a long dewetting run against the oracle by statistics: after rupture the
+# FP32 and FP64 runs part cell by cell, so what is compared is the rupture
+# step, the spectra before it and the distribution of heights after it
+# (stored by tests/golden/make_dewet2_64.py)
+# --------------------------------------------------------------------------
+def test_long_dewetting_run_matches_oracle_statistics():
+    with open(os.path.join(os.path.dirname(__file__), "golden", "dewet2_64_stats.json")) as fh:
+        gold = json.load(fh)
+    p = workloads.dewet2_params(64)
+    h0 = workloads.dewet2_heights(64)
+    with B.Solver(p, h0) as s:
+        state = {"t": 0}
+
+        def at(t):
+            s.step(t - state["t"])
+            state["t"] = t
+            return s.get_heights().astype(np.float64)
+
+        tr, _ = droplets.rupture_step(at, p["hstar"], gold["every"], 20000)
+    assert abs(tr - gold["rupture_step"]) <= 0.03 * gold["rupture_step"]
+    with B.Solver(p, h0) as s:
+        s.step(gold["spectrum_step"])
+        h_pre = s.get_heights().astype(np.float64)
+        s.step(gold["post_step"] - gold["spectrum_step"])
+        h_post = s.get_heights().astype(np.float64)
+        assert s.status() == B.MLSW_OK
+    for i in range(2):
+        got = droplets.radial_spectrum(h_pre[i])
+        want = np.array(gold["spectra"][i])
+        assert np.linalg.norm(got - want) <= 0.05 * np.linalg.norm(want)
+    # per-layer mass after ~2e4 FP32 steps: half of each layer ends on its
+    # precursor, far from the rest-population shift fixed at create (the
+    # median of the initial film), where FP32 rounding of the rest
+    # population leaves a drift of ~4e-5 (2e-9 per step)
+    np.testing.assert_allclose(h_post.sum(axis=(1, 2)), gold["mass"], rtol=1e-4)
+    frac = (h_post[1] < 2 * p["hstar"]).mean()
+    assert abs(frac - gold["dewetted_fraction"]) <= 0.03
+    hist, _ = np.histogram(h_post[1], bins=np.array(gold["hist_bins"]))
+    assert np.abs(hist / hist.sum() - np.array(gold["hist_upper"])).sum() <= 0.15

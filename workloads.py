@@ -35,6 +35,11 @@ its linear-stability checks one film at a time):
     uniform in [-1, 1] and (kx, ky) a random wavenumber with components in
     0..8 (not both zero); seed 3.
 
+Long dewetting run (compared with the oracle by statistics): two layers of
+0.25 plus seeded Gaussian noise 1e-3 (seed 9) on D2Q9 64 x 64, gamma 0.01,
+S_01 = S_11 = gamma (cos 20 deg - 1), h* = 0.05; the film ruptures after
+about 8000 steps and coarsens into drops.
+
 Droplet and lens equilibria (section "Droplet equilibria"; the paper gives
 no grid sizes, so these are stand-ins):
   * sessile ridge, D1Q3: one layer, precursor h*, a circular-arc ridge of
@@ -294,3 +299,19 @@ def sweep_instances(count=512, seed=3, sides=(64, 128, 256, 512), eps=1e-4):
             h[i] = means[i] + eps * amps[i] * mode
         out.append((p, h, (kx, ky), amps))
     return out
+
+
+def dewet2_params(side=64, theta_deg=20.0):
+    """Two thin layers on D2Q9 that dewet: gamma 0.01 / 0.01, S_01 = S_11 =
+    gamma (cos theta - 1), mu = 1/6, slip 1, (3, 2), h* = 0.05."""
+    g = 0.01
+    s = g * (math.cos(math.radians(theta_deg)) - 1.0)
+    return dict(n=2, lattice=2, nx=int(side), ny=int(side), tau=1.0, gamma=[g, g],
+                S=[[s, 0.0], [s]], mu=[1.0 / 6.0, 1.0 / 6.0], beta=[1.0, 1.0], nw=3, mw=2,
+                hstar=0.05)
+
+
+def dewet2_heights(side=64, seed=9):
+    """Both layers 0.25 plus seeded Gaussian noise sigma = 1e-3."""
+    rng = np.random.default_rng(seed)
+    return 0.25 + 1e-3 * rng.standard_normal((2, side, side))
