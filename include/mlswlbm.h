@@ -218,6 +218,17 @@ int mlswlbm_step_until(mlsw_handle* h, long max_steps, long check_every, double 
  * h <= 0 or a non-finite value since create or the last call); clears it. */
 int mlswlbm_status(mlsw_handle* h);
 
+/* Self-test of failure detection, without a GPU fault: one CTA waits on
+ * an mbarrier with the bounded wait the step kernels use for their tile
+ * copies (limit iterations of try_wait, 1 <= limit <= 2^22). With
+ * arrive != 0 the barrier receives its arrival and the call returns
+ * MLSW_OK; with arrive == 0 nothing arrives, every wait runs out, the
+ * kernel records the timeout in a status word and returns, and the call
+ * returns MLSW_ERR_TIMEOUT, the code mlswlbm_status gives when a step's
+ * wait runs out. The CUDA context stays usable. Allocates one int of device
+ * memory; synchronises the stream (cudaStream_t or NULL). */
+int mlswlbm_selftest_bounded_wait(int arrive, unsigned limit, void* stream);
+
 /* Binds another stream to the handle (cudaStream_t or NULL). The caller
  * orders work already queued on the old stream. */
 int mlswlbm_set_stream(mlsw_handle* h, void* stream);

@@ -6,6 +6,7 @@
 #include <cstdint>
 
 #include "kernels.h"
+#include "tma.cuh"
 #include "physics.cuh"
 
 namespace mlsw {
@@ -613,6 +614,32 @@ cudaError_t launch_free_energy(const FreeEnergyParams& E, const float* h, double
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   free_energy_final_kernel<<<1, 32, 0, st>>>(nblk, partials, out);
+  return cudaGetLastError();
+}
+
+}  // namespace mlsw
+
+namespace mlsw {
+
+// ---------------------------------------------------------------------------
+// Self-test of the bounded mbarrier wait of the step kernels: one CTA waits
+// on a barrier that receives its single arrival (arrive != 0) or never does,
+// each thread with the given iteration limit; a wait that runs out sets
+// kStatusTimeout, as a step kernel's does, and the kernel returns.
+// ---------------------------------------------------------------------------
+__global__ void wait_selftest_kernel(int arrive, unsigned limit, int* __restrict__ status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  if (arrive && threadIdx.x == 0) mbar_arrive_expect_tx(&bar, 0u);  // the one arrival, no bytes
+  if (!mbar_wait_bounded(&bar, 0u, limit)) atomicOr(status, kStatusTimeout);
+}
+
+cudaError_t launch_wait_selftest(int arrive, unsigned limit, int* status, cudaStream_t st) {
+  wait_selftest_kernel<<<1, 128, 0, st>>>(arrive, limit, status);
   return cudaGetLastError();
 }
 

@@ -139,6 +139,11 @@ cudaError_t launch_free_energy(const FreeEnergyParams& E, const float* h, double
 cudaError_t launch_friction_eval(const KParams& P, long ncell, const float* h, const float* Jx,
                                  const float* Jy, float* Rx, float* Ry, cudaStream_t st);
 
+// One CTA waits on an mbarrier with the step kernels' bounded wait (limit
+// iterations); the barrier gets its arrival only when arrive != 0. A wait
+// that runs out ORs kStatusTimeout into *status.
+cudaError_t launch_wait_selftest(int arrive, unsigned limit, int* status, cudaStream_t st);
+
 // Dense layout of a caller-owned population array (no ghosts).
 inline Layout dense_layout(int nx, int ny) {
   Layout L;

@@ -686,6 +686,24 @@ int mlswlbm_step_until(mlsw_handle* h, long max_steps, long check_every, double 
   return rc;
 }
 
+int mlswlbm_selftest_bounded_wait(int arrive, unsigned limit, void* stream) {
+  if (limit == 0 || limit > (1u << 22)) return MLSW_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  int* d = nullptr;
+  if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return MLSW_ERR_NOMEM;
+  }
+  int flag = 0;
+  bool ok = cudaMemsetAsync(d, 0, sizeof(int), st) == cudaSuccess &&
+            mlsw::launch_wait_selftest(arrive, limit, d, st) == cudaSuccess &&
+            cudaMemcpyAsync(&flag, d, sizeof(int), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+            cudaStreamSynchronize(st) == cudaSuccess;
+  cudaFree(d);
+  if (!ok) return MLSW_ERR_CUDA;
+  return (flag & mlsw::kStatusTimeout) ? MLSW_ERR_TIMEOUT : MLSW_OK;
+}
+
 int mlswlbm_set_stream(mlsw_handle* h, void* stream) {
   if (!h) return MLSW_ERR_ARG;
   h->stream = (cudaStream_t)stream;

@@ -85,6 +85,7 @@ EXPORTS = {
     "mlswlbm_get_diagnostics": (ctypes.c_int, [_H, _D, _D, _D]),
     "mlswlbm_status": (ctypes.c_int, [_H]),
     "mlswlbm_get_free_energy": (ctypes.c_int, [_H, _D]),
+    "mlswlbm_selftest_bounded_wait": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint, ctypes.c_void_p]),
     "mlswlbm_step_until": (ctypes.c_int, [_H, ctypes.c_long, ctypes.c_long, ctypes.c_double,
                                           ctypes.POINTER(ctypes.c_long), _D]),
     "mlswlbm_set_stream": (ctypes.c_int, [_H, ctypes.c_void_p]),
@@ -496,3 +497,8 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def selftest_bounded_wait(arrive, limit=256, stream=None):
+    """mlswlbm_selftest_bounded_wait: MLSW_OK or MLSW_ERR_TIMEOUT."""
+    return lib().mlswlbm_selftest_bounded_wait(int(bool(arrive)), int(limit), _stream_ptr(stream))

@@ -527,3 +527,19 @@ def test_long_dewetting_run_matches_oracle_statistics():
     assert abs(frac - gold["dewetted_fraction"]) <= 0.03
     hist, _ = np.histogram(h_post[1], bins=np.array(gold["hist_bins"]))
     assert np.abs(hist / hist.sum() - np.array(gold["hist_upper"])).sum() <= 0.15
+
+
+def test_bounded_wait_reports_timeout_and_the_context_survives():
+    # the step kernels wait for their tile copies on an mbarrier with an
+    # iteration limit; here a barrier that never gets its arrival makes the
+    # same wait run out: the kernel records the timeout and returns
+    assert B.selftest_bounded_wait(True, 256) == B.MLSW_OK
+    assert B.selftest_bounded_wait(False, 256) == B.MLSW_ERR_TIMEOUT
+    assert B.selftest_bounded_wait(False, 4096) == B.MLSW_ERR_TIMEOUT
+    # and the CUDA context is fine afterwards
+    p = workloads.film3_d2q9_params(40, 24)
+    h0 = workloads.film3_d2q9_heights(40, 24)
+    with B.Solver(p, h0) as s:
+        s.step(5)
+        assert s.status() == B.MLSW_OK
+    assert B.selftest_bounded_wait(True, 256) == B.MLSW_OK
