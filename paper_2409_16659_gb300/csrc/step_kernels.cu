@@ -160,6 +160,7 @@ template <> struct Lanes<f2> {
 //   ps    [N][TY + 2][34]    p_i on the one-ring region
 //   js    [2][N][TY][32]     fluxes J_i of the tile cells
 //   bar                      mbarrier (8 bytes)
+//   next_tile                (int)
 // About 112 KB per CTA, so two CTAs share an SM and fill each other's
 // barrier waits. With tau = 1 the next tile's copy is issued as soon as the
 // moments are formed and lands while this tile is finished.
@@ -176,11 +177,15 @@ struct D2Tile {
   static constexpr size_t kOffP = kOffZ + (size_t)N * RH * RW * 4;
   static constexpr size_t kOffJ = kOffP + (size_t)N * PH * PW * 4;
   static constexpr size_t kOffBar = (kOffJ + (size_t)2 * N * TY * TX * 4 + 15) / 16 * 16;
-  static constexpr size_t kSmem = kOffBar + 16;
+  // the mbarrier of the stage, then the tile drawn next
+  static constexpr size_t kOffNext = kOffBar + 8;
+  static constexpr size_t kSmem = (kOffNext + 4 + 15) / 16 * 16;
   static_assert(kStageBytes % 128 == 0, "stage alignment");
   static_assert(NHALO <= NT, "one halo cell per thread");
   static_assert(RPT * BY == TY, "tile rows");
-  static_assert(kSmem <= 115712, "two CTAs per SM");
+  // the kernel has no static shared memory: two CTAs and their 1 KB
+  // reserved blocks fill the 228 KB of an SM
+  static_assert(2 * (kSmem + 1024) <= 233472, "two CTAs per SM");
 };
 
 // Kernel modes: the general step for tau != 1 and for tau = 1, and a fast
@@ -234,13 +239,13 @@ __device__ __forceinline__ void d2q9_tile_loop(const Tiles& tiles, int* __restri
   using Ln = Lanes<T>;
   constexpr int W = Ln::W;
   static_assert(RPT == W, "one lane per tile row of the thread");
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   float* stage = reinterpret_cast<float*>(smem_raw);
   float* zs = reinterpret_cast<float*>(smem_raw + Tl::kOffZ);
   float* ps = reinterpret_cast<float*>(smem_raw + Tl::kOffP);
   float* js = reinterpret_cast<float*>(smem_raw + Tl::kOffJ);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + Tl::kOffBar);
-  __shared__ int next_tile;
+  int& next_tile = *reinterpret_cast<int*>(smem_raw + Tl::kOffNext);
 
   const int tid = threadIdx.x;
   const int ntiles = tiles.ntiles;
@@ -324,22 +329,27 @@ __device__ __forceinline__ void d2q9_tile_loop(const Tiles& tiles, int* __restri
                ((v[2] + v[3]) + v[4]) - ((v[6] + v[7]) + v[8]));
       }
     }
-    if (tid < Tl::NHALO) {
-      // halo cells one per thread (sums only), through the same T arithmetic
-      // as the tile cells (both lanes on one cell) so every cell's z has the
-      // same bits whichever tile computes it
-      int r, c;
-      halo_cell(tid, r, c);
-      const float* src = stage + r * BW + (c + 2);
+    // halo cells (sums only), a pair of cells per thread through the same T
+    // arithmetic as the tile cells, so every cell's z has the same bits
+    // whichever tile computes it (with an odd count the last thread puts
+    // one cell in both lanes)
+    constexpr int NH = Tl::NHALO, NHP = (W == 2) ? (NH + 1) / 2 : NH;
+    if (tid < NHP) {
+      int rA, cA, rB, cB;
+      halo_cell(tid, rA, cA);
+      halo_cell((W == 2 && tid + NHP < NH) ? tid + NHP : tid, rB, cB);
+      const float* srcA = stage + rA * BW + (cA + 2);
+      const float* srcB = stage + rB * BW + (cB + 2);
       T z = Num<T>::splat(0.f);
-      if (sub) z = Num<T>::splat(z0_at(c - 2, r - 2));
+      if (sub) z = Ln::ld2(z0_at(cA - 2, rA - 2), z0_at(cB - 2, rB - 2));
 #pragma unroll
       for (int i = 0; i < N; ++i) {
         T v[Q];
 #pragma unroll
-        for (int k = 0; k < Q; ++k) v[k] = Ln::ld(src + (i * Q + k) * BH * BW, src + (i * Q + k) * BH * BW);
+        for (int k = 0; k < Q; ++k)
+          v[k] = Ln::ld(srcA + (i * Q + k) * BH * BW, srcB + (i * Q + k) * BH * BW);
         z += ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
-        zs[(i * RH + r) * RW + c] = Ln::get(z, 0);
+        Ln::st(zs + (i * RH + rA) * RW + cA, zs + (i * RH + rB) * RW + cB, z);
       }
     }
     if (__syncthreads_or(timed_out)) {
@@ -419,9 +429,13 @@ __device__ __forceinline__ void d2q9_tile_loop(const Tiles& tiles, int* __restri
         const int base = (q / Tl::NT) * 2 * Tl::NT + q % Tl::NT;
         pressure_cells(Num<T>::splat(0.f), base, base + Tl::NT);
       }
-      // the rest one cell per thread, through the same T arithmetic (both
-      // lanes on one cell) so a cell's pressure has the same bits in every tile
-      for (int q = NPAIRED + tid; q < NC; q += Tl::NT) pressure_cells(Num<T>::splat(0.f), q, q);
+      // the rest in pairs (q, q + RP), through the same T arithmetic, so a
+      // cell's pressure has the same bits in every tile (with an odd rest the
+      // last pair puts one cell in both lanes)
+      constexpr int R = NC - NPAIRED, RP = (W == 2) ? (R + 1) / 2 : R;
+      for (int j = tid; j < RP; j += Tl::NT)
+        pressure_cells(Num<T>::splat(0.f), NPAIRED + j,
+                       (W == 2 && j + RP < R) ? NPAIRED + j + RP : NPAIRED + j);
     }
     __syncthreads();
     // with tau = 1 written by thread 0 before the barrier above
