@@ -203,6 +203,21 @@ int mlswlbm_get_diagnostics(mlsw_handle* h, double* mass, double* kinetic,
  * runs. Synchronises; status as mlswlbm_get_heights. */
 int mlswlbm_get_free_energy(mlsw_handle* h, double* F);
 
+/* Radially averaged power spectrum of every layer's heights (the quantity
+ * the paper's spinodal-dewetting section follows and sets against its
+ * linear stability analysis): out[i * nbins + b] = mean of |H_i(k)|^2 over
+ * the integer wavevectors k = (kx, ky), kx in (-nx/2, nx/2] and likewise
+ * ky, with round(|k|) = b, for b < nbins; H_i is the unnormalised 2-D DFT of
+ * h_i with its mean removed (0 where a bin holds no wavevector). D1Q3
+ * lattices (ny = 1) give the 1-D spectrum by |kx|. Computed on the device by
+ * FP32 radix-2 FFTs of h_i - H_i (the height minus the layer's
+ * rest-population shift) with FP64 bin sums. nx and ny must be powers of two
+ * up to 8192 and 1 <= nbins <= 8192 (MLSW_ERR_UNSUPPORTED otherwise);
+ * out is host memory of n_layers * nbins doubles. Allocates stream-ordered
+ * scratch of 8 n nx ny bytes for the call (MLSW_ERR_NOMEM if that fails).
+ * Synchronises; returns the handle's status like mlswlbm_get_heights. */
+int mlswlbm_get_spectrum(mlsw_handle* h, int nbins, double* out);
+
 /* Steps until the kinetic energy sum_{i,x} |J_i|^2 / (2 h_i) (as in
  * mlswlbm_get_diagnostics) is below ke_threshold, checked after every
  * check_every >= 1 steps (a run starting from rest has none, so at least

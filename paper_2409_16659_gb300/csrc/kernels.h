@@ -85,6 +85,18 @@ cudaError_t launch_batch_modes(const BatchInst* inst, int count, int cur, const 
 // Heights [n][ny][nx] of one instance (its host descriptor) from buffer cur.
 cudaError_t launch_batch_heights(const BatchInst* inst_host, int cur, float* h, cudaStream_t st);
 
+// Radially averaged power spectra of the layer heights (spectrum.cu): the
+// row and column FFT passes into work (n nx ny complex values), bin sums
+// bins[n][nbins] and wavevector counts counts[nbins], both zeroed by the
+// caller. Power-of-two sides up to kSpectrumMaxSide, 1 <= nbins <=
+// kSpectrumMaxBins.
+constexpr int kSpectrumMaxSide = 8192;
+constexpr int kSpectrumMaxBins = 8192;
+bool spectrum_supported(int nx, int ny, int nbins);
+cudaError_t launch_spectrum(int Q, int n, const Layout& L, const float* f, int nbins,
+                            float2* work, double* bins, unsigned long long* counts,
+                            cudaStream_t st);
+
 // Tile shape of the step kernels (the padded layout covers whole tiles).
 int step_tile_cols(int lattice);
 int step_tile_rows(int n, int lattice);

@@ -665,6 +665,50 @@ int mlswlbm_get_free_energy(mlsw_handle* h, double* F) {
   return mlswlbm_status(h);
 }
 
+int mlswlbm_get_spectrum(mlsw_handle* h, int nbins, double* out) {
+  if (!h || !out || nbins < 1) return MLSW_ERR_ARG;
+  const mlsw_params& p = h->p;
+  if (!mlsw::spectrum_supported(p.nx, p.ny, nbins)) return MLSW_ERR_UNSUPPORTED;
+  const int n = p.n_layers;
+  float2* work = nullptr;
+  double* bins = nullptr;
+  unsigned long long* counts = nullptr;
+  cudaStream_t st = h->stream;
+  const size_t nwork = (size_t)n * p.nx * p.ny;
+  bool ok = cudaMallocAsync(&work, nwork * sizeof(float2), st) == cudaSuccess &&
+            cudaMallocAsync(&bins, (size_t)n * nbins * sizeof(double), st) == cudaSuccess &&
+            cudaMallocAsync(&counts, (size_t)nbins * sizeof(unsigned long long), st) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    if (work) cudaFreeAsync(work, st);
+    if (bins) cudaFreeAsync(bins, st);
+    if (counts) cudaFreeAsync(counts, st);
+    return MLSW_ERR_NOMEM;
+  }
+  std::vector<double> hb((size_t)n * nbins);
+  std::vector<unsigned long long> hc(nbins);
+  ok = cudaMemsetAsync(bins, 0, (size_t)n * nbins * sizeof(double), st) == cudaSuccess &&
+       cudaMemsetAsync(counts, 0, (size_t)nbins * sizeof(unsigned long long), st) == cudaSuccess &&
+       mlsw::launch_spectrum(h->Q, n, h->kp.L, h->f[h->cur], nbins, work, bins, counts, st) ==
+           cudaSuccess &&
+       cudaMemcpyAsync(hb.data(), bins, hb.size() * sizeof(double), cudaMemcpyDeviceToHost, st) ==
+           cudaSuccess &&
+       cudaMemcpyAsync(hc.data(), counts, hc.size() * sizeof(unsigned long long),
+                       cudaMemcpyDeviceToHost, st) == cudaSuccess;
+  cudaFreeAsync(work, st);
+  cudaFreeAsync(bins, st);
+  cudaFreeAsync(counts, st);
+  if (!ok || cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    return MLSW_ERR_CUDA;
+  }
+  h->launches += 2;
+  for (int i = 0; i < n; ++i)
+    for (int b = 0; b < nbins; ++b)
+      out[(size_t)i * nbins + b] = hc[b] ? hb[(size_t)i * nbins + b] / (double)hc[b] : 0.0;
+  return mlswlbm_status(h);
+}
+
 int mlswlbm_step_until(mlsw_handle* h, long max_steps, long check_every, double ke_threshold,
                        long* steps_done, double* kinetic) {
   if (!h || max_steps < 0 || check_every < 1) return MLSW_ERR_ARG;

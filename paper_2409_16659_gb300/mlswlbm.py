@@ -85,6 +85,7 @@ EXPORTS = {
     "mlswlbm_get_diagnostics": (ctypes.c_int, [_H, _D, _D, _D]),
     "mlswlbm_status": (ctypes.c_int, [_H]),
     "mlswlbm_get_free_energy": (ctypes.c_int, [_H, _D]),
+    "mlswlbm_get_spectrum": (ctypes.c_int, [_H, ctypes.c_int, _D]),
     "mlswlbm_selftest_bounded_wait": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint, ctypes.c_void_p]),
     "mlswlbm_step_until": (ctypes.c_int, [_H, ctypes.c_long, ctypes.c_long, ctypes.c_double,
                                           ctypes.POINTER(ctypes.c_long), _D]),
@@ -274,6 +275,18 @@ class Solver:
         F = ctypes.c_double()
         _check(lib().mlswlbm_get_free_energy(self._h, ctypes.byref(F)), "mlswlbm_get_free_energy")
         return F.value
+
+    def spectrum(self, nbins=None):
+        """mlswlbm_get_spectrum: radially averaged power spectrum of every
+        layer, array [n][nbins] (default nbins = min(nx, ny) // 2, or nx // 2
+        for D1Q3)."""
+        nx, ny = self.nx, self.ny
+        if nbins is None:
+            nbins = max(1, (min(nx, ny) if ny > 1 else nx) // 2)
+        out = np.empty((self.n, int(nbins)), dtype=np.float64)
+        _check(lib().mlswlbm_get_spectrum(self._h, int(nbins), out.ctypes.data_as(_D)),
+               "mlswlbm_get_spectrum")
+        return out
 
     def step_until(self, max_steps, check_every, ke_threshold):
         """Steps until the kinetic energy drops below ke_threshold; returns

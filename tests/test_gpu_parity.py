@@ -543,3 +543,71 @@ def test_bounded_wait_reports_timeout_and_the_context_survives():
         s.step(5)
         assert s.status() == B.MLSW_OK
     assert B.selftest_bounded_wait(True, 256) == B.MLSW_OK
+
+
+# --------------------------------------------------------------------------
+# power spectra on the device (mlswlbm_get_spectrum) against the FFT of the
+# read-back heights (tests/droplets.radial_spectrum, pinned on the CPU).
+# The device transforms h - H_i in FP32 (log2 N radix-2 stages, each adding
+# a few u of the transformed signal); the reference transforms, in FP64, the
+# heights as read back, rounded to FP32 (error e <= u |h| / 2 per cell). That
+# rounding moves |H(k)|^2 by at most 2 |H(k)| sqrt(N) e for N cells (the DFT
+# of the rounding field has norm sqrt(N) e per mode on average; 3 sigma), so
+# a bin with power P agrees to 1e-4 P + 6 sqrt(N P) e; bins below 1e-8 of
+# the largest are only bounded.
+# --------------------------------------------------------------------------
+def _check_spectrum(s, h, nbins):
+    got = s.spectrum(nbins)
+    for i in range(h.shape[0]):
+        f = h[i] if h.ndim == 3 else h[i][None, :]
+        want = droplets.radial_spectrum(f, nbins)
+        e = np.finfo(np.float32).eps * np.abs(f).max() / 2
+        tol = 1e-4 * want + 6 * np.sqrt(f.size * want) * e
+        big = want > 1e-8 * want.max()
+        assert np.all(np.abs(got[i] - want)[big] <= tol[big]), i
+        assert np.all(np.abs(got[i] - want)[~big] <= 1e-6 * want.max()), i
+
+
+@pytest.mark.parametrize("nx,ny", [(128, 128), (256, 64), (64, 512)])
+def test_spectrum_matches_fft_of_read_back_heights(nx, ny):
+    p = workloads.film3_d2q9_params(nx, ny)
+    h0 = workloads.film3_d2q9_heights(nx, ny, seed=4)
+    with B.Solver(p, h0) as s:
+        s.step(300)
+        h = s.get_heights().astype(np.float64)
+        _check_spectrum(s, h, min(nx, ny) // 2)
+        _check_spectrum(s, h, 7)
+
+
+def test_spectrum_d1q3_and_a_single_mode():
+    p = workloads.film2_d1q3_params(512)
+    h0 = workloads.film2_d1q3_heights(512)
+    with B.Solver(p, h0) as s:
+        s.step(200)
+        _check_spectrum(s, s.get_heights().astype(np.float64), 256)
+    # one cosine mode (3, 4) of amplitude a on layer 2 only: all its power
+    # sits in bin 5, |H(k)|^2 = (a N / 2)^2 at k = +-(3, 4)
+    nx = ny = 64
+    p = workloads.film3_d2q9_params(nx, ny)
+    y, x = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    a = 1e-3
+    h = np.stack([np.full((ny, nx), 1.0), 0.8 + a * np.cos(2 * np.pi * (3 * x / nx + 4 * y / ny)),
+                  np.full((ny, nx), 0.6)])
+    with B.Solver(p, h) as s:
+        sp = s.spectrum(32)
+        counts = np.bincount(np.rint(np.hypot(*np.meshgrid(np.fft.fftfreq(nx) * nx,
+                                                           np.fft.fftfreq(ny) * ny))).astype(int).ravel())
+        want5 = 2 * (a * nx * ny / 2) ** 2 / counts[5]
+        assert abs(sp[1, 5] - want5) <= 1e-4 * want5
+        others = np.delete(sp[1], 5)
+        assert others.max() <= 1e-8 * want5
+        assert sp[0].max() <= 1e-8 * want5 and sp[2].max() <= 1e-8 * want5
+
+
+def test_spectrum_rejects_unsupported_sizes():
+    p = workloads.film3_d2q9_params(96, 64)
+    with B.Solver(p, workloads.film3_d2q9_heights(96, 64)) as s:
+        with pytest.raises(B.MlswError) as err:
+            s.spectrum(16)
+        assert err.value.code == B.MLSW_ERR_UNSUPPORTED
+        assert s.status() == B.MLSW_OK
