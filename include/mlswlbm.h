@@ -218,6 +218,34 @@ int mlswlbm_get_free_energy(mlsw_handle* h, double* F);
  * Synchronises; returns the handle's status like mlswlbm_get_heights. */
 int mlswlbm_get_spectrum(mlsw_handle* h, int nbins, double* out);
 
+/* Azimuthal averages of the interface heights around (cx, cy), the
+ * profiles the paper's droplet-equilibrium section fits circular arcs to:
+ * out[m * nbins + b] = mean of z_m over the cells whose periodic
+ * (minimum-image) distance r from (cx, cy) has floor(r) = b, for the
+ * interfaces m = 0..n (z_0 the substrate, z_m = z_0 + h_1 + ... + h_m) and
+ * b < nbins; 0 for an empty ring. counts (optional, nbins values) receives
+ * the cells per ring. Per-cell heights are those of mlswlbm_get_heights
+ * (FP32); interfaces and ring sums are FP64, summed on the device. D2Q9
+ * only (MLSW_ERR_UNSUPPORTED otherwise); MLSW_ERR_ARG for nbins < 1 or a
+ * non-finite centre. out is host memory of (n_layers + 1) * nbins doubles.
+ * Allocates stream-ordered scratch for the call; synchronises; returns the
+ * handle's status like mlswlbm_get_heights. */
+int mlswlbm_get_radial_profile(mlsw_handle* h, double cx, double cy, int nbins, double* out,
+                               long long* counts);
+
+/* Contact angle of an axisymmetric cap (the paper's droplet-equilibrium
+ * fit), host only: the circular arc through the profile's apex prof[0] at
+ * r = 0 that meets the level `base` at angle theta; theta minimises the
+ * relative volume difference E = sum_b a_b |prof_b - arc(r_b)| /
+ * sum_b a_b (prof_b - base), r_b = b + 1/2, a_b = area[b] (the cells per
+ * ring). Scan from 0.5 to 60 degrees in 0.05-degree steps, then 40
+ * golden-section steps between the neighbours of the best one. Writes theta
+ * in degrees and, if err is not NULL, E. MLSW_ERR_ARG for NULL arrays,
+ * nbins < 2 or prof[0] <= base. For a lens, pass the upper surface above its
+ * far level, or the far level minus the lower surface, with base 0. */
+int mlswlbm_fit_cap_angle(const double* prof, const double* area, int nbins, double base,
+                          double* theta_deg, double* err);
+
 /* Steps until the kinetic energy sum_{i,x} |J_i|^2 / (2 h_i) (as in
  * mlswlbm_get_diagnostics) is below ke_threshold, checked after every
  * check_every >= 1 steps (a run starting from rest has none, so at least

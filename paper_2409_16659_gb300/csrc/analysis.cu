@@ -1,7 +1,12 @@
-// spectrum.cu -- radially averaged power spectra of the layer heights, the
-// quantity the paper's spinodal-dewetting section follows in time and
-// compares with the growth rates of its linear stability analysis.
+// analysis.cu -- analysis of a solver's state on the device:
+//   * radially averaged power spectra of the layer heights, the quantity the
+//     paper's spinodal-dewetting section follows in time and compares with
+//     the growth rates of its linear stability analysis;
+//   * azimuthal averages of the interface heights around a drop or lens
+//     centre, the profiles its droplet-equilibrium section fits circular
+//     arcs to.
 //
+// Spectra.
 // S_i(b) = mean of |H_i(k)|^2 over the integer wavevectors k = (kx, ky),
 // kx in (-nx/2, nx/2] and likewise ky, with round(|k|) = b, where H_i is the
 // unnormalised 2-D DFT of h_i with its mean removed (the k = 0 term is set
@@ -158,6 +163,65 @@ cudaError_t launch_spectrum(int Q, int n, const Layout& L, const float* f, int n
   if (e != cudaSuccess) return e;
   spectrum_cols_kernel<<<dim3(nx / cb, n), 256, col_smem, st>>>(nx, ny, by, cb, work, nbins, bins,
                                                                 counts);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Azimuthal averages of the interface heights z_0 .. z_n (z_0 the substrate)
+// in unit-width rings b = floor(r) around (cx, cy), r the periodic
+// (minimum-image) distance; per-cell heights as the read-out gives them
+// (h_i = H_i + sum of the stored populations, in FP32), interfaces and sums
+// in FP64. One thread per cell, FP64 atomics into sums[m][nbins] and
+// counts[nbins].
+// ---------------------------------------------------------------------------
+template <int Q>
+__global__ void __launch_bounds__(256)
+    radial_profile_kernel(int n, Layout L, const float* __restrict__ f, KShift sh,
+                          ProfileParams A, double* __restrict__ sums,
+                          unsigned long long* __restrict__ counts) {
+  const int nx = L.nx, ny = L.ny;
+  const long cell = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= (long)nx * ny) return;
+  const int y = (int)(cell / nx), x = (int)(cell - (long)y * nx);
+  double dx = x - A.cx, dy = y - A.cy;
+  dx -= nx * rint(dx / nx);
+  dy -= ny * rint(dy / ny);
+  const double r = sqrt(dx * dx + dy * dy);
+  if (!(r < (double)A.nbins)) return;
+  const int b = (int)floor(r);
+  double z = 0.0;
+  if (A.sub_amp != 0.0) {
+    // z_0 = a cos(2 pi (kx x / nx + ky y / ny)), phase reduced in integers
+    const long nc = (long)nx * ny;
+    long m = (((long)A.sub_kx * x) % nx) * ny + (((long)A.sub_ky * y) % ny) * nx;
+    m %= nc;
+    if (m < 0) m += nc;
+    z = A.sub_amp * cospi(2.0 * (double)m / (double)nc);
+  }
+  atomicAdd(sums + b, z);
+  for (int i = 0; i < n; ++i) {
+    const float* src = f + L.at(i * Q, x, y);
+    float d = 0.f;
+#pragma unroll
+    for (int k = 0; k < Q; ++k) d += src[(long)k * L.plane];
+    z += (double)(sh.H[i] + d);
+    atomicAdd(sums + (long)(i + 1) * A.nbins + b, z);
+  }
+  atomicAdd(counts + b, 1ull);
+}
+
+cudaError_t launch_radial_profile(int Q, int n, const Layout& L, const float* f, const KShift& sh,
+                                  const ProfileParams& A, double* sums,
+                                  unsigned long long* counts, cudaStream_t st) {
+  const long cells = (long)L.nx * L.ny;
+  if (A.nbins < 1 || n < 1 || cells < 1) return cudaErrorInvalidValue;
+  const unsigned grid = (unsigned)((cells + 255) / 256);
+  if (Q == 9)
+    radial_profile_kernel<9><<<grid, 256, 0, st>>>(n, L, f, sh, A, sums, counts);
+  else if (Q == 3)
+    radial_profile_kernel<3><<<grid, 256, 0, st>>>(n, L, f, sh, A, sums, counts);
+  else
+    return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 

@@ -85,7 +85,7 @@ cudaError_t launch_batch_modes(const BatchInst* inst, int count, int cur, const 
 // Heights [n][ny][nx] of one instance (its host descriptor) from buffer cur.
 cudaError_t launch_batch_heights(const BatchInst* inst_host, int cur, float* h, cudaStream_t st);
 
-// Radially averaged power spectra of the layer heights (spectrum.cu): the
+// Radially averaged power spectra of the layer heights (analysis.cu): the
 // row and column FFT passes into work (n nx ny complex values), bin sums
 // bins[n][nbins] and wavevector counts counts[nbins], both zeroed by the
 // caller. Power-of-two sides up to kSpectrumMaxSide, 1 <= nbins <=
@@ -96,6 +96,19 @@ bool spectrum_supported(int nx, int ny, int nbins);
 cudaError_t launch_spectrum(int Q, int n, const Layout& L, const float* f, int nbins,
                             float2* work, double* bins, unsigned long long* counts,
                             cudaStream_t st);
+
+// Azimuthal averages of the interfaces around (cx, cy) (analysis.cu):
+// sums[m][nbins] of z_m and counts[nbins] of cells per unit-width ring,
+// both zeroed by the caller; z_0 the substrate of the given parameters.
+struct ProfileParams {
+  double cx, cy;
+  int nbins;
+  double sub_amp;
+  int sub_kx, sub_ky;
+};
+cudaError_t launch_radial_profile(int Q, int n, const Layout& L, const float* f, const KShift& sh,
+                                  const ProfileParams& A, double* sums,
+                                  unsigned long long* counts, cudaStream_t st);
 
 // Tile shape of the step kernels (the padded layout covers whole tiles).
 int step_tile_cols(int lattice);

@@ -709,6 +709,108 @@ int mlswlbm_get_spectrum(mlsw_handle* h, int nbins, double* out) {
   return mlswlbm_status(h);
 }
 
+int mlswlbm_get_radial_profile(mlsw_handle* h, double cx, double cy, int nbins, double* out,
+                               long long* counts) {
+  if (!h || !out || nbins < 1 || !std::isfinite(cx) || !std::isfinite(cy)) return MLSW_ERR_ARG;
+  if (h->p.lattice != MLSW_D2Q9) return MLSW_ERR_UNSUPPORTED;
+  const int n = h->p.n_layers;
+  const size_t nsum = (size_t)(n + 1) * nbins;
+  cudaStream_t st = h->stream;
+  double* sums = nullptr;
+  unsigned long long* cnt = nullptr;
+  bool ok = cudaMallocAsync(&sums, nsum * sizeof(double), st) == cudaSuccess &&
+            cudaMallocAsync(&cnt, (size_t)nbins * sizeof(unsigned long long), st) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    if (sums) cudaFreeAsync(sums, st);
+    if (cnt) cudaFreeAsync(cnt, st);
+    return MLSW_ERR_NOMEM;
+  }
+  mlsw::ProfileParams A;
+  A.cx = cx;
+  A.cy = cy;
+  A.nbins = nbins;
+  A.sub_amp = h->p.sub_amp;
+  A.sub_kx = h->p.sub_kx;
+  A.sub_ky = h->p.sub_ky;
+  std::vector<double> hs(nsum);
+  std::vector<unsigned long long> hc(nbins);
+  ok = cudaMemsetAsync(sums, 0, nsum * sizeof(double), st) == cudaSuccess &&
+       cudaMemsetAsync(cnt, 0, (size_t)nbins * sizeof(unsigned long long), st) == cudaSuccess &&
+       mlsw::launch_radial_profile(h->Q, n, h->kp.L, h->f[h->cur], h->sh, A, sums, cnt, st) ==
+           cudaSuccess &&
+       cudaMemcpyAsync(hs.data(), sums, nsum * sizeof(double), cudaMemcpyDeviceToHost, st) ==
+           cudaSuccess &&
+       cudaMemcpyAsync(hc.data(), cnt, (size_t)nbins * sizeof(unsigned long long),
+                       cudaMemcpyDeviceToHost, st) == cudaSuccess;
+  cudaFreeAsync(sums, st);
+  cudaFreeAsync(cnt, st);
+  if (!ok || cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    return MLSW_ERR_CUDA;
+  }
+  h->launches += 1;
+  for (int m = 0; m <= n; ++m)
+    for (int b = 0; b < nbins; ++b)
+      out[(size_t)m * nbins + b] = hc[b] ? hs[(size_t)m * nbins + b] / (double)hc[b] : 0.0;
+  if (counts)
+    for (int b = 0; b < nbins; ++b) counts[b] = (long long)hc[b];
+  return mlswlbm_status(h);
+}
+
+namespace {
+
+// relative volume difference between a radial profile and the circular arc
+// of angle theta through its apex prof[0] meeting the level base
+double cap_error(const double* prof, const double* area, int nbins, double base, double theta) {
+  const double rc = (prof[0] - base) / (1.0 - std::cos(theta));
+  double num = 0.0, den = 0.0;
+  for (int b = 0; b < nbins; ++b) {
+    const double r = b + 0.5;
+    const double inside = std::sqrt(std::max(rc * rc - r * r, 0.0));
+    const double arc = base + std::max(0.0, inside - rc * std::cos(theta));
+    num += area[b] * std::fabs(prof[b] - arc);
+    den += area[b] * (prof[b] - base);
+  }
+  return num / den;
+}
+
+}  // namespace
+
+int mlswlbm_fit_cap_angle(const double* prof, const double* area, int nbins, double base,
+                          double* theta_deg, double* err) {
+  if (!prof || !area || nbins < 2 || !theta_deg || !(prof[0] > base)) return MLSW_ERR_ARG;
+  constexpr double kDeg = 3.14159265358979323846 / 180.0;
+  // scan 0.5 .. 60 degrees in 0.05-degree steps, then golden section between
+  // the neighbours of the best step
+  const int nscan = 1190;
+  int best = 0;
+  double ebest = 0.0;
+  for (int j = 0; j < nscan; ++j) {
+    const double e = cap_error(prof, area, nbins, base, (0.5 + 0.05 * j) * kDeg);
+    if (j == 0 || e < ebest) {
+      ebest = e;
+      best = j;
+    }
+  }
+  double a = (0.5 + 0.05 * std::max(best - 1, 0)) * kDeg;
+  double b = (0.5 + 0.05 * std::min(best + 1, nscan - 1)) * kDeg;
+  const double g = (std::sqrt(5.0) - 1.0) / 2.0;
+  double c = b - g * (b - a), d = a + g * (b - a);
+  for (int it = 0; it < 40; ++it) {
+    if (cap_error(prof, area, nbins, base, c) < cap_error(prof, area, nbins, base, d))
+      b = d;
+    else
+      a = c;
+    c = b - g * (b - a);
+    d = a + g * (b - a);
+  }
+  const double t = 0.5 * (a + b);
+  *theta_deg = t / kDeg;
+  if (err) *err = cap_error(prof, area, nbins, base, t);
+  return MLSW_OK;
+}
+
 int mlswlbm_step_until(mlsw_handle* h, long max_steps, long check_every, double ke_threshold,
                        long* steps_done, double* kinetic) {
   if (!h || max_steps < 0 || check_every < 1) return MLSW_ERR_ARG;

@@ -86,6 +86,10 @@ EXPORTS = {
     "mlswlbm_status": (ctypes.c_int, [_H]),
     "mlswlbm_get_free_energy": (ctypes.c_int, [_H, _D]),
     "mlswlbm_get_spectrum": (ctypes.c_int, [_H, ctypes.c_int, _D]),
+    "mlswlbm_get_radial_profile": (ctypes.c_int, [_H, ctypes.c_double, ctypes.c_double,
+                                                  ctypes.c_int, _D,
+                                                  ctypes.POINTER(ctypes.c_longlong)]),
+    "mlswlbm_fit_cap_angle": (ctypes.c_int, [_D, _D, ctypes.c_int, ctypes.c_double, _D, _D]),
     "mlswlbm_selftest_bounded_wait": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint, ctypes.c_void_p]),
     "mlswlbm_step_until": (ctypes.c_int, [_H, ctypes.c_long, ctypes.c_long, ctypes.c_double,
                                           ctypes.POINTER(ctypes.c_long), _D]),
@@ -287,6 +291,17 @@ class Solver:
         _check(lib().mlswlbm_get_spectrum(self._h, int(nbins), out.ctypes.data_as(_D)),
                "mlswlbm_get_spectrum")
         return out
+
+    def radial_profile(self, centre, nbins):
+        """mlswlbm_get_radial_profile: ring means of the interfaces z_0..z_n
+        around centre = (cx, cy), array [n + 1][nbins], and the cells per
+        ring [nbins]."""
+        out = np.empty((self.n + 1, int(nbins)), dtype=np.float64)
+        cnt = np.empty(int(nbins), dtype=np.int64)
+        _check(lib().mlswlbm_get_radial_profile(
+            self._h, float(centre[0]), float(centre[1]), int(nbins), out.ctypes.data_as(_D),
+            cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong))), "mlswlbm_get_radial_profile")
+        return out, cnt
 
     def step_until(self, max_steps, check_every, ke_threshold):
         """Steps until the kinetic energy drops below ke_threshold; returns
@@ -515,3 +530,17 @@ class Batch:
 def selftest_bounded_wait(arrive, limit=256, stream=None):
     """mlswlbm_selftest_bounded_wait: MLSW_OK or MLSW_ERR_TIMEOUT."""
     return lib().mlswlbm_selftest_bounded_wait(int(bool(arrive)), int(limit), _stream_ptr(stream))
+
+
+def fit_cap_angle(profile, area, base):
+    """mlswlbm_fit_cap_angle: (theta in degrees, E) of the arc fit to a
+    radial profile with ring areas `area` above the level `base`."""
+    prof = np.ascontiguousarray(profile, dtype=np.float64)
+    ar = np.ascontiguousarray(area, dtype=np.float64)
+    if ar.size != prof.size:
+        raise ValueError("one area per ring")
+    th, e = ctypes.c_double(), ctypes.c_double()
+    _check(lib().mlswlbm_fit_cap_angle(prof.ctypes.data_as(_D), ar.ctypes.data_as(_D),
+                                       int(prof.size), float(base), ctypes.byref(th),
+                                       ctypes.byref(e)), "mlswlbm_fit_cap_angle")
+    return th.value, e.value

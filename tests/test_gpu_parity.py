@@ -679,3 +679,40 @@ def test_spectrum_growth_follows_the_linearised_step():
         big = want > 1e-4 * want.max()
         assert np.all(np.abs(got[i] - want)[big] <= 1e-2 * want[big]), (i, got[i][big] / want[big])
         assert np.all(np.abs(got[i] - want)[~big] <= 1e-4 * want.max()), i
+
+
+def test_radial_profiles_on_the_device_and_the_library_cap_fit():
+    """mlswlbm_get_radial_profile equals the azimuthal means of the read-back
+    interfaces (tests/droplets.radial_profile) ring by ring, substrate
+    included, and the library's arc fit on those profiles gives the lens
+    angles of the host helper that the oracle comparison uses."""
+    side, radius = 128, 12.5
+    p = workloads.lens3_params(side, side, radius)
+    h0 = workloads.lens3_heights(side, side, radius)
+    for sub in (False, True):
+        q = dict(p, sub_amp=0.05, sub_kx=1, sub_ky=2) if sub else p
+        with B.Solver(q, h0) as s:
+            s.step(3000)
+            h = s.get_heights().astype(np.float64)
+            y, x = np.meshgrid(np.arange(side), np.arange(side), indexing="ij")
+            z0 = 0.05 * np.cos(2 * np.pi * (x / side + 2 * y / side)) if sub else np.zeros_like(h[0])
+            z = np.concatenate([z0[None], z0[None] + np.cumsum(h, axis=0)])
+            nb = int(1.6 * radius)
+            for c in workloads.lens3_centres(side, side, radius):
+                cc = droplets.peak_centre(h[2], c, int(radius))
+                prof, cnt = s.radial_profile(cc, nb)
+                for m in range(4):
+                    rad, want, area = droplets.radial_profile(z[m], cc, nb)
+                    assert np.array_equal(cnt, area.astype(np.int64))
+                    np.testing.assert_allclose(prof[m], want, rtol=1e-12, atol=1e-13)
+                if sub:
+                    continue
+                # upper and lower opening angles, as tests/droplets.lens3_angles forms them
+                (up_ref, lo_ref), = droplets.lens3_angles(h, [c], radius)
+                up = prof[3] - prof[3][-3:].mean()
+                lo = prof[2][-3:].mean() - prof[2]
+                t_up, e_up = B.fit_cap_angle(up, cnt, 0.0)
+                t_lo, e_lo = B.fit_cap_angle(lo, cnt, 0.0)
+                assert abs(t_up - up_ref[0]) < 1e-6 and abs(e_up - up_ref[1]) < 1e-9
+                assert abs(t_lo - lo_ref[0]) < 1e-6 and abs(e_lo - lo_ref[1]) < 1e-9
+            assert s.status() == B.MLSW_OK
