@@ -8,7 +8,9 @@ Parameters are plain dicts (the same data the CUDA binding receives):
     n, lattice (1 = D1Q3, 2 = D2Q9), nx, ny, tau,
     gamma[n]  (gamma_{i,i+1}), S[i][k-1] (S_{ik}, i = 0..n-1, k = 1..n-i),
     mu[n], beta[n], nw, mw, hstar, and optionally a sinusoidal substrate
-    sub_amp, sub_kx, sub_ky (z_0 = sub_amp cos 2 pi (kx x / nx + ky y / ny)).
+    sub_amp, sub_kx, sub_ky (z_0 = sub_amp cos 2 pi (kx x / nx + ky y / ny))
+    and the wetting potential's kind: wet_kind 0 (the power law with
+    exponents nw, mw) or 1 (exponential, decay rate kappa).
 Arrays are float64 numpy arrays in the layouts documented in oracle.h.
 """
 import ctypes
@@ -39,6 +41,8 @@ class orc_params(ctypes.Structure):
         ("sub_amp", ctypes.c_double),
         ("sub_kx", ctypes.c_int),
         ("sub_ky", ctypes.c_int),
+        ("wet_kind", ctypes.c_int),
+        ("kappa", ctypes.c_double),
     ]
 
 
@@ -101,6 +105,8 @@ def make_params(p: dict) -> orc_params:
     s.mw = int(p["mw"])
     s.hstar = float(p["hstar"])
     s.sub_amp = float(p.get("sub_amp", 0.0))
+    s.wet_kind = int(p.get("wet_kind", 0))
+    s.kappa = float(p.get("kappa", 0.0))
     s.sub_kx = int(p.get("sub_kx", 0))
     s.sub_ky = int(p.get("sub_ky", 0))
     return s

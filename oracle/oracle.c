@@ -80,15 +80,25 @@ void orc_lattice(const orc_params* P, int* cx, int* cy, double* w) {
 /* ------------------------------------------------------------------ */
 /* wetting potential, Eq. (wetting_potential)                          */
 /*   phi_k(h) = [nw r^mw - mw r^nw] / (nw - mw), r = k hstar / h        */
+/* or, for charged surfaces (wet_kind 1), with a = e^{-kappa (h - k h*)} */
+/*   phi_k(h) = 2 a - a^2                                               */
 /* ------------------------------------------------------------------ */
 double orc_phi(const orc_params* P, int k, double h) {
+  if (P->wet_kind == 1) {
+    double a = exp(-P->kappa * (h - (double)k * P->hstar));
+    return 2.0 * a - a * a;
+  }
   double r = (double)k * P->hstar / h;
   double n = (double)P->nw, m = (double)P->mw;
   return (n * pow(r, m) - m * pow(r, n)) / (n - m);
 }
 
-/* d/dh of the above: d(r^a)/dh = -a r^a / h */
+/* d/dh of the above: d(r^a)/dh = -a r^a / h; da/dh = -kappa a */
 double orc_dphi(const orc_params* P, int k, double h) {
+  if (P->wet_kind == 1) {
+    double a = exp(-P->kappa * (h - (double)k * P->hstar));
+    return (2.0 - 2.0 * a) * (-P->kappa * a);
+  }
   double r = (double)k * P->hstar / h;
   double n = (double)P->nw, m = (double)P->mw;
   return (n * (-m * pow(r, m) / h) - m * (-n * pow(r, n) / h)) / (n - m);

@@ -48,6 +48,12 @@ typedef struct {
      sub_amp = 0 is the flat substrate of the paper's runs */
   double sub_amp;
   int sub_kx, sub_ky;
+  /* wetting potential: 0 = the power law of Eq. (wetting_potential) with
+     exponents (nw, mw); 1 = the exponential decay the paper quotes for
+     charged surfaces, phi_k(d) = 2 e^{-kappa (d - k h*)} - e^{-2 kappa (d - k h*)},
+     with the same limits phi_k(k h*) = 1, phi_k'(k h*) = 0, phi_k -> 0 */
+  int wet_kind;
+  double kappa;
 } orc_params;
 
 /* wetting potential phi_k(h) and its derivative, Eq. (wetting_potential) */

@@ -36,19 +36,34 @@ def lattice(p):
     return D1Q3 if int(p["lattice"]) == 1 else D2Q9
 
 
+def _exp_a(p, k, h):
+    """a = e^{-kappa (h - k h*)} of the exponential (charged-surface) form
+    phi_k = 2 a - a^2 (wet_kind 1)."""
+    return np.exp(-p["kappa"] * (h - k * p["hstar"]))
+
+
 def phi_k(p, k, h):
+    if int(p.get("wet_kind", 0)) == 1:
+        a = _exp_a(p, k, h)
+        return 2 * a - a * a
     a = k * p["hstar"] / h
     n, m = p["nw"], p["mw"]
     return (n * a ** m - m * a ** n) / (n - m)
 
 
 def dphi_k(p, k, h):
+    if int(p.get("wet_kind", 0)) == 1:
+        a = _exp_a(p, k, h)  # da/dh = -kappa a
+        return 2 * p["kappa"] * a * (a - 1)
     a = k * p["hstar"] / h
     n, m = p["nw"], p["mw"]
     return n * m / (n - m) * (a ** n - a ** m) / h
 
 
 def ddphi_k(p, k, h):
+    if int(p.get("wet_kind", 0)) == 1:
+        a = _exp_a(p, k, h)
+        return 2 * p["kappa"] ** 2 * a * (1 - 2 * a)
     a = k * p["hstar"] / h
     n, m = p["nw"], p["mw"]
     return n * m / (n - m) * (-(n + 1) * a ** n + (m + 1) * a ** m) / h ** 2
