@@ -78,7 +78,8 @@ extern "C" {
  *   mu[i-1]         viscosity mu_i > 0.
  *   beta[i-1]       slip length beta_i >= 0 of Eq. (no_slip): beta_1 at the
  *                   substrate, beta_{i>1} at the interface below layer i.
- *   wet_n, wet_m    exponents of Eq. (wetting_potential), wet_n > wet_m >= 1.
+ *   wet_n, wet_m    exponents of Eq. (wetting_potential), wet_n > wet_m >= 1
+ *                   (with wet_kind 0, the power law).
  *   hstar           precursor thickness h* > 0.
  *   tau             BGK relaxation time of Eq. (BGK), tau > 1/2 (paper: 1).
  *   nx, ny          periodic lattice size; D1Q3 needs ny == 1.
@@ -104,6 +105,14 @@ typedef struct mlsw_params {
    * Eq. (disjoining_pressure). D1Q3 needs sub_ky = 0. */
   double sub_amp;
   int sub_kx, sub_ky;
+  /* wetting potential: wet_kind 0 is the power law of Eq. (wetting_potential)
+   * with exponents (wet_n, wet_m); 1 is the exponential decay the paper
+   * quotes for charged surfaces (the discussion before that ansatz), in the
+   * form phi_k(d) = 2 e^{-kappa (d - k h*)} - e^{-2 kappa (d - k h*)} with
+   * kappa = wet_kappa > 0. It keeps the power law's limits phi_k(k h*) = 1,
+   * phi_k'(k h*) = 0 and phi_k -> 0, and wet_n, wet_m are not used. */
+  int wet_kind;
+  double wet_kappa;
 } mlsw_params;
 
 typedef struct mlsw_handle mlsw_handle;

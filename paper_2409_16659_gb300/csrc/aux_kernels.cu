@@ -520,6 +520,10 @@ namespace mlsw {
 constexpr int kFreeThreads = 256;
 
 __device__ __forceinline__ double phi_d(const FreeEnergyParams& E, int k, double h) {
+  if (E.wet_kind == 1) {
+    const double a = exp(-E.kappa * (h - k * E.hstar));
+    return 2.0 * a - a * a;
+  }
   const double r = k * E.hstar / h;
   return (E.nw * pow(r, (double)E.mw) - E.mw * pow(r, (double)E.nw)) / (double)(E.nw - E.mw);
 }

@@ -156,6 +156,8 @@ struct FreeEnergyParams {
   int nw, mw;
   double sub_amp;  // substrate z_0 = sub_amp cos(2 pi (kx x / nx + ky y / ny))
   int sub_kx, sub_ky;
+  int wet_kind;    // 0 power law (nw, mw), 1 exponential (kappa)
+  double kappa;
 };
 cudaError_t launch_free_energy(const FreeEnergyParams& E, const float* h, double* partials,
                                int nblk, double* out, cudaStream_t st);

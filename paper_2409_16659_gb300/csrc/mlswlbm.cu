@@ -133,8 +133,12 @@ KParams make_kparams(const mlsw_params& p) {
   k.hstar = (float)p.hstar;
   k.nw = p.wet_n;
   k.mw = p.wet_m;
-  k.c_phi = (float)(1.0 / (p.wet_n - p.wet_m));
-  k.c_dphi = (float)((double)p.wet_n * p.wet_m / (p.wet_n - p.wet_m));
+  if (p.wet_kind == 0) {
+    k.c_phi = (float)(1.0 / (p.wet_n - p.wet_m));
+    k.c_dphi = (float)((double)p.wet_n * p.wet_m / (p.wet_n - p.wet_m));
+  }
+  k.wet_kind = p.wet_kind;
+  k.kappa = (float)p.wet_kappa;
   k.sub_amp = (float)p.sub_amp;
   k.sub_kx = p.sub_kx;
   k.sub_ky = p.sub_ky;
@@ -382,7 +386,10 @@ int mlswlbm_check_params(const mlsw_params* p) {
   if (cells > 4.0e9) return MLSW_ERR_ARG;  // 32-bit tile indexing limit, 16 GB per buffer
   if (!std::isfinite(p->tau) || !(p->tau > 0.5)) return MLSW_ERR_ARG;
   if (!finite_pos(p->hstar)) return MLSW_ERR_ARG;
-  if (p->wet_m < 1 || p->wet_n <= p->wet_m || p->wet_n > 64) return MLSW_ERR_ARG;
+  if (p->wet_kind != 0 && p->wet_kind != 1) return MLSW_ERR_ARG;
+  if (p->wet_kind == 0 && (p->wet_m < 1 || p->wet_n <= p->wet_m || p->wet_n > 64))
+    return MLSW_ERR_ARG;
+  if (p->wet_kind == 1 && !finite_pos(p->wet_kappa)) return MLSW_ERR_ARG;
   if (!std::isfinite(p->sub_amp)) return MLSW_ERR_ARG;
   if (p->sub_amp != 0.0 && p->lattice == MLSW_D1Q3 && p->sub_ky != 0) return MLSW_ERR_ARG;
   for (int i = 0; i < n; ++i) {
@@ -655,6 +662,8 @@ int mlswlbm_get_free_energy(mlsw_handle* h, double* F) {
   E.hstar = p.hstar;
   E.nw = p.wet_n;
   E.mw = p.wet_m;
+  E.wet_kind = p.wet_kind;
+  E.kappa = p.wet_kappa;
   E.sub_amp = p.sub_amp;
   E.sub_kx = p.sub_kx;
   E.sub_ky = p.sub_ky;

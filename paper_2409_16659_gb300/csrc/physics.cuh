@@ -67,6 +67,10 @@ struct KParams {
   // sub_amp = 0 is the flat substrate
   float sub_amp;
   int sub_kx, sub_ky;
+  // wetting potential: 0 the power law (nw, mw), 1 the charged-surface form
+  // phi_k(d) = 2 a - a^2, a = e^{-kappa (d - k h*)}
+  int wet_kind;
+  float kappa;
 };
 
 // Substrate height at lattice cell (x, y) (any integers: the cosine is
@@ -151,6 +155,8 @@ __device__ __forceinline__ f2 fmav(f2 a, float b, float c) { return fmav(a, mk2(
 // 1e2) arguments used here: layer thicknesses, friction pivots)
 __device__ __forceinline__ float rcp(float x) { return __fdividef(1.f, x); }
 __device__ __forceinline__ f2 rcp(f2 x) { return mk2(rcp(x.v.x), rcp(x.v.y)); }
+__device__ __forceinline__ float expv(float x) { return expf(x); }
+__device__ __forceinline__ f2 expv(f2 x) { return mk2(expf(x.v.x), expf(x.v.y)); }
 
 template <class T>
 __device__ __forceinline__ T ipow(T r, int e) {
@@ -213,13 +219,22 @@ __device__ __forceinline__ void layer_pressures_dev(const KParams& P, const T (&
       const float s = P.S[l][k - 1];
       if (NN || s != 0.f) {
         const T d = (zd[m - 1] - zl) + P.Hsum[l][m];
-        const T inv_d = rcp(d);
-        const T r = ((float)k * P.hstar) * inv_d;
-        T rm, rn;
-        wet_powers<W32>(P, r, rm, rn);
-        const T phi = W32 ? fmav(rm, 3.f, -2.f * rn)
-                          : (fmav(rm, (float)P.nw, -(float)P.mw * rn)) * P.c_phi;
-        const T dphi = (P.c_dphi * (rn - rm)) * inv_d;
+        T phi, dphi;
+        if (!W32 && P.wet_kind == 1) {
+          // charged surfaces: a = e^{-kappa (d - k h*)}, phi = 2 a - a^2,
+          // phi' = 2 kappa a (a - 1)
+          const T a = expv(fmav(d, -P.kappa, P.kappa * ((float)k * P.hstar)));
+          phi = a * (2.f - a);
+          dphi = (2.f * P.kappa) * (a * (a - 1.f));
+        } else {
+          const T inv_d = rcp(d);
+          const T r = ((float)k * P.hstar) * inv_d;
+          T rm, rn;
+          wet_powers<W32>(P, r, rm, rn);
+          phi = W32 ? fmav(rm, 3.f, -2.f * rn)
+                    : (fmav(rm, (float)P.nw, -(float)P.mw * rn)) * P.c_phi;
+          dphi = (P.c_dphi * (rn - rm)) * inv_d;
+        }
         const T se = s * dphi;
         // explicit fused updates, so one cell and a packed pair of cells
         // round identically

@@ -879,7 +879,7 @@ static cudaError_t launch_d2(const StepLaunch& a, cudaStream_t st) {
 
 int step_mode(const KParams& P) {
   if (P.omega != 1.f) return kGeneral;
-  const bool w32 = (P.nw == 3 && P.mw == 2);
+  const bool w32 = (P.wet_kind == 0 && P.nw == 3 && P.mw == 2);
   bool nn = true;  // spreading coefficients only between neighbouring interfaces
   for (int l = 0; l < P.n; ++l)
     for (int k = 2; k <= P.n - l; ++k) nn = nn && (P.S[l][k - 1] == 0.f);
@@ -945,7 +945,7 @@ cudaError_t launch_batch_step(const BatchLaunch& a, cudaStream_t st) {
 template <int N>
 static cudaError_t launch_n(const StepLaunch& a, cudaStream_t st) {
   const bool tau1 = (a.P.omega == 1.f);
-  const bool w32 = (a.P.nw == 3 && a.P.mw == 2);
+  const bool w32 = (a.P.wet_kind == 0 && a.P.nw == 3 && a.P.mw == 2);
   if (a.lattice == 2) {
     switch (step_mode(a.P)) {
       case kGeneral: return launch_d2<N, kGeneral>(a, st);
@@ -983,7 +983,7 @@ static cudaError_t launch_d1p(const StepLaunch& a, int nsteps, cudaStream_t st) 
 template <int N>
 static cudaError_t launch_d1p_n(const StepLaunch& a, int nsteps, cudaStream_t st) {
   const bool tau1 = (a.P.omega == 1.f);
-  const bool w32 = (a.P.nw == 3 && a.P.mw == 2);
+  const bool w32 = (a.P.wet_kind == 0 && a.P.nw == 3 && a.P.mw == 2);
   if (tau1) return w32 ? launch_d1p<N, true, true>(a, nsteps, st) : launch_d1p<N, true, false>(a, nsteps, st);
   return launch_d1p<N, false, false>(a, nsteps, st);
 }

@@ -6,7 +6,9 @@ CPU path.
 
 Parameter dicts (also accepted by the oracle) use the keys
     n, lattice (1 = D1Q3, 2 = D2Q9), nx, ny, tau, gamma[n], S[i][k-1],
-    mu[n], beta[n], nw, mw, hstar (and optional flags).
+    mu[n], beta[n], nw, mw, hstar (and optional flags, a sinusoidal
+    substrate sub_amp, sub_kx, sub_ky, and the wetting potential's kind
+    wet_kind 0 = power law, 1 = exponential with decay rate kappa).
 Host arrays are numpy float32 (or anything numpy can view as such);
 device arrays are torch CUDA tensors (float32, contiguous). PyTorch is used
 only for device memory and streams.
@@ -55,6 +57,8 @@ class mlsw_params(ctypes.Structure):
         ("sub_amp", ctypes.c_double),
         ("sub_kx", ctypes.c_int),
         ("sub_ky", ctypes.c_int),
+        ("wet_kind", ctypes.c_int),
+        ("wet_kappa", ctypes.c_double),
     ]
 
 
@@ -169,6 +173,8 @@ def make_params(p):
     s.sub_amp = float(p.get("sub_amp", 0.0))
     s.sub_kx = int(p.get("sub_kx", 0))
     s.sub_ky = int(p.get("sub_ky", 0))
+    s.wet_kind = int(p.get("wet_kind", 0))
+    s.wet_kappa = float(p.get("kappa", 0.0))
     return s
 
 

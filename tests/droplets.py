@@ -151,7 +151,8 @@ def lens3_angles(h, centres, radius):
 def free_energy(p, h):
     """Free energy of Eq. (free_energy_n_layer), long-wave form, from heights
     [n][ny][nx] with the lattice gradient of the step (isotropic stencil on
-    D2Q9, central difference on D1Q3); S_ik phi_k for the wetting terms; the
+    D2Q9, central difference on D1Q3); S_ik phi_k for the wetting terms (the
+    power law, or the exponential form when p["wet_kind"] == 1); the
     substrate z_0 of the parameters (sinusoidal, or flat)."""
     n = int(p["n"])
     ny, nx = int(p["ny"]), int(p["nx"])
@@ -178,6 +179,9 @@ def free_energy(p, h):
     hs, nw, mw = float(p["hstar"]), int(p["nw"]), int(p["mw"])
 
     def phi(k, t):
+        if int(p.get("wet_kind", 0)) == 1:  # charged surfaces: 2 a - a^2
+            a = np.exp(-float(p["kappa"]) * (t - k * hs))
+            return 2 * a - a * a
         r = k * hs / t
         return (nw * r ** mw - mw * r ** nw) / (nw - mw)
 

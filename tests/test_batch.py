@@ -32,6 +32,10 @@ def _mixed_instances():
     # on a corrugated substrate
     p = dict(workloads.random_params(17, 3, B.MLSW_D2Q9, 48, 32), sub_amp=0.1, sub_kx=2, sub_ky=1)
     out.append((p, workloads.random_heights(117, p)))
+    # with the exponential (charged-surface) wetting potential
+    p = workloads.random_params(18, 2, B.MLSW_D2Q9, 40, 40)
+    p.update(wet_kind=1, kappa=1.0 / p["hstar"])
+    out.append((p, workloads.random_heights(118, p)))
     return out
 
 

@@ -101,6 +101,41 @@ def test_random_params_multistep(n):
     assert _relmax(hg, hr) <= 1e-5
 
 
+# the exponential (charged-surface) wetting potential, decay length h*:
+# every layer count, both lattices, tau = 1 and tau != 1
+EXP_ONE_STEP = [(n, lat, tau) for n in (1, 2, 3, 5) for lat, tau in ((2, 1.0), (2, 0.8), (1, 1.0))]
+
+
+@pytest.mark.parametrize("n,lat,tau", EXP_ONE_STEP)
+def test_one_step_with_the_exponential_potential(n, lat, tau):
+    p, f = one_step_case(n, lat, tau)
+    p = dict(p, wet_kind=1, kappa=1.0 / p["hstar"])
+    hmax = oracle.heights(p, f).max()
+    with B.Solver(p, oracle.heights(p, f)) as s:
+        s.set_state(f)
+        s.step(1)
+        fg = s.get_state().astype(np.float64)
+        assert s.status() == B.MLSW_OK
+    fr = oracle.step(p, f)
+    assert np.abs(fg - fr).max() <= 4e-6 * hmax
+
+
+def test_exponential_potential_multistep_and_free_energy():
+    p, h0 = multistep_case(3)
+    p = dict(p, wet_kind=1, kappa=1.0 / p["hstar"])
+    hg, hr = _run_both(p, h0, 300)
+    assert _relmax(hg, hr) <= 1e-5
+    # the power law ends 7e-5 away: the bound above tells the two forms apart
+    q = dict(p, wet_kind=0)
+    hp = oracle.heights(q, oracle.run(q, oracle.init(q, _f32(h0).ravel()), 300))
+    assert _relmax(hp.reshape(hr.shape), hr) > 3e-5
+    with B.Solver(p, h0) as s:
+        s.step(50)
+        F = s.free_energy()
+        want = droplets.free_energy(p, s.get_heights().astype(np.float64))
+    assert F == pytest.approx(want, rel=1e-10, abs=1e-12)
+
+
 @pytest.mark.parametrize("lat,nx,ny", EDGE)
 def test_degenerate_and_edge_sizes(lat, nx, ny):
     p, h0 = edge_case(lat, nx, ny)
