@@ -31,7 +31,9 @@ Two more workloads are reported beside the main line, under "workloads"
     autotuner: LSU/s of the batched step, the time to solution of 2000
     steps with the perturbed mode measured every 200 steps and a growth
     rate fitted per instance, and the same steps run instance by instance
-    with one solver each (20 steps per instance, scaled to 2000).
+    with one solver each (20 steps per instance, scaled to 2000);
+  * analysis on the device, 1024^2 film: radial power spectra of the layers
+    and ring means of the interfaces, wall time per call.
 
 Reference arm (--impl reference): the FP64 CPU oracle on the host cores, one
 oracle step per benchmark step on a 128 x 128 patch with the same recipe.
@@ -392,7 +394,8 @@ def run_own(args):
 
 
 def extra_workloads(B, torch):
-    """Time to solution of the D1Q3 film and LSU/s of the 2048^2 lens field."""
+    """Time to solution of the D1Q3 film, LSU/s of the 2048^2 lens field and
+    of the batched sweep, and the analysis calls on the 1024^2 film."""
     out = {}
     p = workloads.film2_d1q3_params(512)
     h0 = workloads.film2_d1q3_heights(512)
@@ -430,7 +433,33 @@ def extra_workloads(B, torch):
             "l2": "back-to-back steps; 2 x 906 MB working set > 129 MB L2",
             "status": B.mlswlbm_strerror(s.status())}
     out["stability_sweep_512"] = sweep_workload(B, torch)
+    out["analysis_film3_1024"] = analysis_workload(B)
     return out
+
+
+def analysis_workload(B):
+    """Wall time of the on-device analysis calls on the 1024^2 three-layer
+    film: radial power spectra of the three layers (512 bins) and the ring
+    means of the four interfaces around the centre (300 rings), each call
+    including its read-back."""
+    p = workloads.film3_d2q9_params(NX, NY)
+    h0 = workloads.film3_d2q9_heights(NX, NY, seed=2)
+    with B.Solver(p, h0) as s:
+        s.step(100)
+        s.spectrum(NX // 2)
+        s.radial_profile((NX / 2, NY / 2), 300)
+        reps = 10
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            s.spectrum(NX // 2)
+        t1 = time.perf_counter()
+        for _ in range(reps):
+            s.radial_profile((NX / 2, NY / 2), 300)
+        t2 = time.perf_counter()
+        return {"spectrum_ms": 1e3 * (t1 - t0) / reps, "radial_profile_ms": 1e3 * (t2 - t1) / reps,
+                "note": "mlswlbm_get_spectrum(512 bins) and mlswlbm_get_radial_profile(300 rings), "
+                        "wall clock per call, results on the host",
+                "status": B.mlswlbm_strerror(s.status())}
 
 
 def sweep_workload(B, torch):

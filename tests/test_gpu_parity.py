@@ -751,3 +751,40 @@ def test_radial_profiles_on_the_device_and_the_library_cap_fit():
                 assert abs(t_up - up_ref[0]) < 1e-6 and abs(e_up - up_ref[1]) < 1e-9
                 assert abs(t_lo - lo_ref[0]) < 1e-6 and abs(e_lo - lo_ref[1]) < 1e-9
             assert s.status() == B.MLSW_OK
+
+
+def test_analysis_edge_cases():
+    """More bins than wavevectors or cells reach (empty bins are 0), a
+    centre outside the box (periodic distances), one-row and tiny lattices,
+    and argument errors that leave the handle usable."""
+    p = workloads.film3_d2q9_params(32, 16)
+    h0 = workloads.film3_d2q9_heights(32, 16, seed=3)
+    with B.Solver(p, h0) as s:
+        s.step(20)
+        h = s.get_heights().astype(np.float64)
+        sp = s.spectrum(64)  # |k| reaches round(sqrt(16^2 + 8^2)) = 18
+        for i in range(3):
+            want = droplets.radial_spectrum(h[i], 64)
+            np.testing.assert_allclose(sp[i, :19], want[:19], rtol=1e-3, atol=1e-6 * want.max())
+            assert np.all(sp[i, 19:] == 0)
+        z = np.concatenate([np.zeros((1, 16, 32)), np.cumsum(h, axis=0)])
+        for c in [(-3.5, 40.25), (31.0, 15.0), (100.0, -20.0)]:
+            prof, cnt = s.radial_profile(c, 40)
+            for m in range(4):
+                _, want, area = droplets.radial_profile(z[m], np.mod(c, (32, 16)), 40)
+                np.testing.assert_allclose(prof[m], want, rtol=1e-12, atol=1e-13)
+            assert cnt.sum() == 32 * 16 and np.all(cnt[20:] == 0)
+        with pytest.raises(B.MlswError) as err:
+            s.radial_profile((0.0, 0.0), 0)
+        assert err.value.code == B.MLSW_ERR_ARG
+        with pytest.raises(B.MlswError) as err:
+            s.spectrum(0)
+        assert err.value.code == B.MLSW_ERR_ARG
+        assert s.status() == B.MLSW_OK
+    # D1Q3: spectra yes, ring profiles no
+    p = workloads.film2_d1q3_params(64)
+    with B.Solver(p, workloads.film2_d1q3_heights(64)) as s:
+        assert s.spectrum(32).shape == (2, 32)
+        with pytest.raises(B.MlswError) as err:
+            s.radial_profile((10.0, 0.0), 8)
+        assert err.value.code == B.MLSW_ERR_UNSUPPORTED
