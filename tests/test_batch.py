@@ -130,3 +130,27 @@ def test_single_mode_follows_linearised_step_in_a_batch(seed, n, mode):
             got = b.modes([mode[0], 0], [mode[1], 0])[0, :n] / side ** 2
             want = (np.linalg.matrix_power(G, t) @ v).reshape(n, Q).sum(axis=1)
             assert np.abs(got - want).max() <= 2e-3 * np.abs(want).max() + 1e-9, (t, got, want)
+
+
+def test_full_size_stability_sweep_sampled_against_oracle():
+    """The 512-instance stability sweep of the bench in its launch
+    configuration (autotuned tile heights, the step replayed as a CUDA
+    graph): after 20 steps, the smallest and the largest instance of every
+    layer count equal the FP64 oracle to 1e-5 of their largest height."""
+    import oracle
+    inst = workloads.sweep_instances()
+    picks = []
+    for n in (2, 3, 4, 5):
+        js = [j for j, (p, *_r) in enumerate(inst) if p["n"] == n]
+        picks.append(min(js, key=lambda j: inst[j][0]["nx"]))
+        picks.append(max(js, key=lambda j: inst[j][0]["nx"]))
+    with B.Batch([p for p, *_r in inst], [h for _p, h, *_r in inst],
+                 flags=B.MLSW_BATCH_AUTOTUNE) as b:
+        b.step(20)
+        assert b.status() == B.MLSW_OK
+        for j in picks:
+            p, h0 = inst[j][0], inst[j][1]
+            hg = b.get_heights(j).astype(np.float64)
+            f = oracle.run(p, oracle.init(p, h0.astype(np.float64).ravel()), 20)
+            hr = oracle.heights(p, f).reshape(hg.shape)
+            assert np.abs(hg - hr).max() <= 1e-5 * np.abs(hr).max(), (j, p["n"], p["nx"])

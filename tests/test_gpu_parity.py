@@ -214,6 +214,23 @@ def test_full_size_film3_1024_in_bench_configuration():
     assert np.abs(fg - fr).max() <= 3 * 4e-6 * hmax
 
 
+def test_full_size_lens3_2048_in_bench_configuration():
+    """The 2048 x 2048 three-layer lens field of the bench workloads (lenses
+    of radius 200 on two flat layers, steep rims), in its launch
+    configuration: three steps from the initial state, every population of
+    the 12.6 M layer-sites compared with the oracle."""
+    side, radius = 2048, 200.0
+    p = workloads.lens3_params(side, side, radius)
+    h0 = _f32(workloads.lens3_heights(side, side, radius))
+    with B.Solver(p, h0) as s:
+        s.step(3)
+        fg = s.get_state().astype(np.float64)
+        assert s.status() == B.MLSW_OK
+    fr = oracle.run(p, oracle.init(p, h0.ravel()), 3)
+    hmax = h0.max()
+    assert np.abs(fg - fr).max() <= 3 * 4e-6 * hmax
+
+
 def test_nonfinite_state_is_reported():
     p = workloads.film3_d2q9_params(40, 20)
     h0 = workloads.film3_d2q9_heights(40, 20)
