@@ -50,6 +50,15 @@ def test_film2_d1q3_512_cells_1000_steps():
     assert _relmax(hg, hr) <= 1e-5
 
 
+def test_film2_d1q3_512_cells_10000_steps():
+    """The two-layer D1Q3 film at its full length, 10 000 steps (one
+    persistent launch on the GPU): heights within 1e-5 of the oracle's."""
+    p = workloads.film2_d1q3_params(512)
+    h0 = workloads.film2_d1q3_heights(512)
+    hg, hr = _run_both(p, h0, 10000)
+    assert _relmax(hg, hr) <= 1e-5
+
+
 def test_film3_d2q9_ragged_1000_steps():
     # 72 x 40 cells: 3 x 3 tiles of 32 x 16, ragged in both directions
     p = workloads.film3_d2q9_params(72, 40)
