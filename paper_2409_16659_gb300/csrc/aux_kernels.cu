@@ -207,11 +207,14 @@ cudaError_t launch_fill_ghosts(int nplanes, const Layout& L, bool ghosts_y, floa
 template <int Q, int V>
 __global__ void __launch_bounds__(kRowThreads)
     heights_kernel(int n, Layout L, const float* __restrict__ f, KShift sh,
-                   float* __restrict__ h) {
+                   float* __restrict__ h, const int* __restrict__ st_in,
+                   int* __restrict__ st_out) {
   using Rw = Row<V>;
   using T = typename Rw::T;
   const int nx = L.nx, ny = L.ny;
   const int x = (blockIdx.x * blockDim.x + threadIdx.x) * V;
+  // the status word of the steps before, to its host mirror
+  if (st_out && x == 0 && blockIdx.y == 0) *st_out = *st_in;
   if (x >= nx) return;
   for (long r = blockIdx.y; r < (long)n * ny; r += gridDim.y) {
     const int i = (int)(r / ny), y = (int)(r - (long)i * ny);
@@ -229,24 +232,25 @@ __global__ void __launch_bounds__(kRowThreads)
 
 template <int Q>
 static void heights_q(const dim3& g, int V, int n, const Layout& L, const float* f,
-                      const KShift& sh, float* h, cudaStream_t st) {
+                      const KShift& sh, float* h, const int* st_in, int* st_out,
+                      cudaStream_t st) {
   if (V == 4)
-    heights_kernel<Q, 4><<<g, kRowThreads, 0, st>>>(n, L, f, sh, h);
+    heights_kernel<Q, 4><<<g, kRowThreads, 0, st>>>(n, L, f, sh, h, st_in, st_out);
   else
-    heights_kernel<Q, 1><<<g, kRowThreads, 0, st>>>(n, L, f, sh, h);
+    heights_kernel<Q, 1><<<g, kRowThreads, 0, st>>>(n, L, f, sh, h, st_in, st_out);
 }
 
 cudaError_t launch_heights(int Q, int n, const Layout& L, const float* f, const KShift& sh,
-                           float* h, cudaStream_t st) {
+                           float* h, cudaStream_t st, const int* st_in, int* st_out) {
   const bool vec = L.nx % 4 == 0 && (reinterpret_cast<uintptr_t>(h) & 15) == 0 &&
                    (reinterpret_cast<uintptr_t>(f) & 15) == 0 && L.pitch % 4 == 0 &&
                    L.gx % 4 == 0 && L.plane % 4 == 0;
   const int V = vec ? 4 : 1;
   const dim3 g = row_grid(L.nx / V, (long)n * L.ny);
   if (Q == 9)
-    heights_q<9>(g, V, n, L, f, sh, h, st);
+    heights_q<9>(g, V, n, L, f, sh, h, st_in, st_out, st);
   else if (Q == 3)
-    heights_q<3>(g, V, n, L, f, sh, h, st);
+    heights_q<3>(g, V, n, L, f, sh, h, st_in, st_out, st);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();

@@ -128,8 +128,12 @@ cudaError_t launch_fill_ghosts(int nplanes, const Layout& L, bool ghosts_y, floa
                                cudaStream_t st);
 
 // h dense [n][ny][nx] = H_i + sum_k g[i][k]
+// With st_out (a device view of page-locked host memory), the first thread
+// also copies the status word *st_in there, so that the host reads it after
+// the synchronisation it needs anyway.
 cudaError_t launch_heights(int Q, int n, const Layout& L, const float* f, const KShift& sh,
-                           float* h, cudaStream_t st);
+                           float* h, cudaStream_t st, const int* st_in = nullptr,
+                           int* st_out = nullptr);
 
 // real cells of the rest planes: f[i][0] += sign * H_i
 cudaError_t launch_shift(int Q, int n, const Layout& L, float* f, const KShift& sh, float sign,

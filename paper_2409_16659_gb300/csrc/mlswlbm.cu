@@ -34,6 +34,8 @@ struct mlsw_handle {
   int num_sms;
   size_t psmem;       // D1Q3 persistent launch: shared memory bytes (0: not used)
   CUtensorMap map[2]; // D2Q9: tensor map of each buffer, box = one tile + halo
+  int* status_host;   // page-locked mirror of status[0], written by the read-out
+  int* status_mirror; // its device address
 };
 
 namespace mlsw_host {
@@ -411,6 +413,7 @@ void mlswlbm_destroy(mlsw_handle* h) {
   cudaFree(h->status);
   cudaFree(h->partials);
   cudaFree(h->dout);
+  if (h->status_host) cudaFreeHost(h->status_host);
   delete h;
 }
 
@@ -458,7 +461,9 @@ int mlswlbm_create(const mlsw_params* p, const float* h_init, void* stream, mlsw
             cudaMalloc(&h->status, 4 * sizeof(int)) == cudaSuccess &&
             cudaMalloc(&h->partials, (size_t)h->nblk_diag * (n + 2) * sizeof(double)) ==
                 cudaSuccess &&
-            cudaMalloc(&h->dout, (size_t)(n + 2) * sizeof(double)) == cudaSuccess;
+            cudaMalloc(&h->dout, (size_t)(n + 2) * sizeof(double)) == cudaSuccess &&
+            cudaHostAlloc(&h->status_host, sizeof(int), cudaHostAllocMapped) == cudaSuccess &&
+            cudaHostGetDevicePointer(&h->status_mirror, h->status_host, 0) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     mlswlbm_destroy(h);
@@ -569,15 +574,21 @@ int mlswlbm_get_heights_device(mlsw_handle* h, float* dev_out) {
 
 int mlswlbm_get_heights(mlsw_handle* h, float* out) {
   if (!h || !out) return MLSW_ERR_ARG;
-  // page-locked output is written by the read-out kernel in place
+  // page-locked output is written by the read-out kernel in place; the
+  // kernel also mirrors the status word to the host, so one
+  // synchronisation serves both
   float* mapped = static_cast<float*>(const_cast<void*>(mapped_host_ptr(out)));
-  int rc = mlswlbm_get_heights_device(h, mapped ? mapped : h->hbuf);
-  if (rc != MLSW_OK) return rc;
+  CU(mlsw::launch_heights(h->Q, h->p.n_layers, h->kp.L, h->f[h->cur], h->sh,
+                          mapped ? mapped : h->hbuf, h->stream, h->status, h->status_mirror));
+  h->launches += 1;
   if (!mapped) {
     const size_t bytes = (size_t)h->p.n_layers * h->ncell * sizeof(float);
     CU(cudaMemcpyAsync(out, h->hbuf, bytes, cudaMemcpyDeviceToHost, h->stream));
   }
-  return mlswlbm_status(h);
+  CU(cudaStreamSynchronize(h->stream));
+  const int flag = *static_cast<volatile int*>(h->status_host);
+  if (!flag) return MLSW_OK;
+  return mlswlbm_status(h);  // reports the flag and clears it
 }
 
 int mlswlbm_get_state(mlsw_handle* h, float* f_out) {
