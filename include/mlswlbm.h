@@ -393,6 +393,59 @@ int mlswlbm_batch_groups(const mlsw_batch* b);
 
 void mlswlbm_batch_destroy(mlsw_batch* b);
 
+/* ---------------------------------------------------------------------
+ * Surrogate of 64 LBM steps: a small convolutional network that maps the
+ * layer heights h(t) of a periodic lattice to h(t + 64 steps), trained on
+ * trajectories of the solver. Three 5 x 5 convolutions with periodic
+ * padding, 16 -> 32 -> 32 -> 16 channels, ReLU between them; the input
+ * channels are h_i - mean(h_i) times in_scale (zero channels up to 16), the
+ * first n outputs the change over 64 steps times out_scale. The predicted
+ * change is made mean-free per layer, so the prediction conserves every
+ * layer's mass like the LBM does. BF16 weights and activations, FP32
+ * accumulation on the tensor cores (warp-level mma.sync); FP32 master
+ * parameters and Adam moments. All arrays are device memory in the layout
+ * of mlswlbm_get_heights_device ([batch][n][ny][nx] FP32) unless stated;
+ * work is enqueued on the stream given at create.
+ * ------------------------------------------------------------------- */
+typedef struct mlswlbm_surrogate mlswlbm_surrogate;
+
+/* Number of FP32 parameters (weights [d][in][out] of the three layers, then
+ * their biases). */
+long mlswlbm_surrogate_param_count(void);
+
+/* Creates a network for n_layers (1..MLSW_MAX_LAYERS) on nx x ny lattices
+ * (nx a multiple of 16) and batches of up to max_batch samples; He-normal
+ * weights from a generator seeded with `seed`, zero biases. MLSW_ERR_ARG,
+ * MLSW_ERR_NOMEM; *out is NULL on failure. */
+int mlswlbm_surrogate_create(int n_layers, int nx, int ny, int max_batch, unsigned long long seed,
+                             double in_scale, double out_scale, void* stream,
+                             mlswlbm_surrogate** out);
+
+/* out = h + the predicted, mass-projected change over 64 steps, for `batch`
+ * samples (device arrays; out may not alias h). Asynchronous. */
+int mlswlbm_surrogate_predict(mlswlbm_surrogate* s, const float* h, float* out, int batch);
+
+/* One Adam step (learning rate lr, betas 0.9 / 0.999) on the mean squared
+ * error between the network's change and (target - h) out_scale over the n
+ * layers; *loss (optional, host) receives that error before the step and
+ * then the call synchronises. */
+int mlswlbm_surrogate_train_step(mlswlbm_surrogate* s, const float* h, const float* target,
+                                 int batch, double lr, double* loss);
+
+/* Parameters to / from host memory (count = mlswlbm_surrogate_param_count());
+ * setting them also resets the Adam moments. Synchronise. */
+int mlswlbm_surrogate_set_params(mlswlbm_surrogate* s, const float* host, long count);
+int mlswlbm_surrogate_get_params(mlswlbm_surrogate* s, float* host, long count);
+
+/* Copies an internal buffer of the last forward / training pass to host
+ * memory, for tests: 0 network output (FP32 [pixel][16]), 1 parameter
+ * gradient (FP32), 2 input (BF16 [pixel][16]), 3 and 4 hidden activations
+ * (BF16 [pixel][32]), 5 output gradient (BF16 [pixel][16]), 6 and 7 the
+ * gradients of the hidden activations (second, then first). Synchronises. */
+int mlswlbm_surrogate_debug(mlswlbm_surrogate* s, int what, void* out, long bytes);
+
+void mlswlbm_surrogate_destroy(mlswlbm_surrogate* s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -15,7 +15,7 @@ CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libmlswlbm.so")
 SOURCES = ["mlswlbm.cu", "step_kernels.cu", "aux_kernels.cu", "noalloc.cu", "batch.cu",
-           "analysis.cu"]
+           "analysis.cu", "surrogate.cu"]
 HEADERS = ["physics.cuh", "kernels.h", "tma.cuh", "host.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
