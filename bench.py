@@ -33,7 +33,11 @@ Two more workloads are reported beside the main line, under "workloads"
     rate fitted per instance, and the same steps run instance by instance
     with one solver each (20 steps per instance, scaled to 2000);
   * analysis on the device, 1024^2 film: radial power spectra of the layers
-    and ring means of the interfaces, wall time per call.
+    and ring means of the interfaces, wall time per call;
+  * the convolutional surrogate of 64 LBM steps on the 64^2 two-layer
+    dewetting film: training on solver trajectories, held-out errors against
+    the LBM and the identity map, time per window, a rollout with LBM
+    fallback.
 
 Reference arm (--impl reference): the FP64 CPU oracle on the host cores, one
 oracle step per benchmark step on a 128 x 128 patch with the same recipe.
@@ -434,7 +438,79 @@ def extra_workloads(B, torch):
             "status": B.mlswlbm_strerror(s.status())}
     out["stability_sweep_512"] = sweep_workload(B, torch)
     out["analysis_film3_1024"] = analysis_workload(B)
+    out["surrogate_dewet2_64"] = surrogate_workload(B, torch)
     return out
+
+
+def surrogate_workload(B, torch):
+    """The convolutional surrogate of 64 LBM steps on the two-layer 64^2
+    dewetting film: trajectories of 64 seeded instances (150 windows of 64
+    steps, through rupture), 6000 training steps on 56 of them, errors on the
+    other 8 against the LBM and against the identity map, time per window,
+    and a rollout that falls back to the LBM when the predicted change
+    exceeds the threshold calibrated on the training windows."""
+    from paper_2409_16659_gb300 import surrogate as S
+    side, ninst, nwin = 64, 64, 150
+    params = [workloads.dewet2_params(side) for _ in range(ninst)]
+    heights = [workloads.dewet2_heights(side, seed=100 + j).astype(np.float32) for j in range(ninst)]
+    res = {}
+    t0 = time.perf_counter()
+    traj = S.trajectories(params, heights, nwin)
+    torch.cuda.synchronize()
+    res["trajectories_s"] = time.perf_counter() - t0
+    train_idx, test_idx = list(range(56)), list(range(56, 64))
+    late = slice(90, None)  # windows from step 5760 on: rupture and coarsening
+    with B.Surrogate(2, side, side, 32, seed=1, in_scale=10.0, out_scale=40.0) as s:
+        t0 = time.perf_counter()
+        losses = S.train(s, traj, train_idx, 6000, 32, 2e-3, 1e-4, seed=2)
+        res["train_s"] = time.perf_counter() - t0
+        res["loss_start_end"] = [float(losses[:20].mean()), float(losses[-50:].mean())]
+        err, ident, _ = S.window_errors(s, traj, test_idx)
+        etr, _, ctr = S.window_errors(s, traj, train_idx[:16])
+        res["held_out"] = {
+            "frac_windows_err_le_1e-3": float((err <= 1e-3).mean()),
+            "identity_frac_le_1e-3": float((ident <= 1e-3).mean()),
+            "nonlinear_median_err": float(np.median(err[:, late])),
+            "identity_nonlinear_median": float(np.median(ident[:, late])),
+            "nonlinear_frac_le_1e-3": float((err[:, late] <= 1e-3).mean())}
+        h1 = traj[56:57, 100].contiguous()
+        o1 = torch.empty_like(h1)
+        h32 = traj[24:56, 100].contiguous()
+        o32 = torch.empty_like(h32)
+        for _ in range(5):
+            s.predict(h1, o1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(50):
+            s.predict(h1, o1)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for _ in range(20):
+            s.predict(h32, o32)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        with B.Solver(params[0], heights[0]) as lbm:
+            lbm.step(S.WINDOW)
+            torch.cuda.synchronize()
+            t3 = time.perf_counter()
+            for _ in range(20):
+                lbm.step(S.WINDOW)
+            torch.cuda.synchronize()
+            t4 = time.perf_counter()
+        res["window_us"] = {"surrogate_1": 1e6 * (t1 - t0) / 50,
+                            "surrogate_per_sample_in_32": 1e6 * (t2 - t1) / 20 / 32,
+                            "lbm_64_steps": 1e6 * (t4 - t3) / 20}
+        tau = S.calibrate(etr, ctr)
+        hr, taken, secs = S.rollout(s, params[60], heights[60], nwin, tau)
+        hl, secs_l = S.lbm_rollout(params[60], heights[60], nwin)
+        hs = params[60]["hstar"]
+        res["rollout"] = {"windows": nwin, "tau": tau, "surrogate_windows": taken,
+                          "s": secs, "lbm_only_s": secs_l,
+                          "surrogate_stats": S.film_statistics(hr, hs),
+                          "lbm_stats": S.film_statistics(hl, hs)}
+    res["note"] = ("errors are the largest height difference per window of 64 steps; the "
+                   "nonlinear windows start at step 5760, before rupture (~7200)")
+    return res
 
 
 def analysis_workload(B):

@@ -132,3 +132,28 @@ def test_training_learns_a_linear_smoothing():
             h, t = batch()
             losses.append(s.train_step(torch.from_numpy(h).cuda(), torch.from_numpy(t).cuda(), 2e-3))
         assert np.mean(losses[-20:]) < 0.05 * np.mean(losses[:5])
+
+
+def test_trained_on_dewetting_trajectories_it_beats_the_identity():
+    """Trained for a short while on trajectories of the dewetting film, the
+    surrogate predicts the held-out nonlinear windows (rupture and after)
+    closer to the LBM than no change does, and its predictions keep every
+    layer's mass."""
+    import workloads
+    from paper_2409_16659_gb300 import surrogate as S
+    side, ninst, nwin = 64, 20, 130
+    params = [workloads.dewet2_params(side) for _ in range(ninst)]
+    heights = [workloads.dewet2_heights(side, seed=300 + j).astype(np.float32) for j in range(ninst)]
+    traj = S.trajectories(params, heights, nwin)
+    with B.Surrogate(2, side, side, 32, seed=3, in_scale=10.0, out_scale=40.0) as s:
+        losses = S.train(s, traj, list(range(16)), 1500, 32, 2e-3, 2e-4, seed=4)
+        assert losses[-50:].mean() < 0.2 * losses[:20].mean()
+        err, ident, _ = S.window_errors(s, traj, list(range(16, 20)))
+        late = slice(100, None)
+        assert np.median(err[:, late]) < 0.6 * np.median(ident[:, late])
+        h = traj[16:20, 110].contiguous()
+        out = torch.empty_like(h)
+        s.predict(h, out)
+        m0 = h.double().sum(dim=(2, 3))
+        m1 = out.double().sum(dim=(2, 3))
+        assert float((m1 - m0).abs().max()) <= 1e-6 * float(m0.abs().max())
