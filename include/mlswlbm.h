@@ -166,6 +166,12 @@ int mlswlbm_get_heights(mlsw_handle* h, float* out);
  * handle's device); asynchronous, no status check. */
 int mlswlbm_get_heights_device(mlsw_handle* h, float* dev_out);
 
+/* Restarts the state from heights in device memory (n*nx*ny floats,
+ * [layer][y][x], on the handle's device): f = f_eq(h, U = 0), as
+ * mlswlbm_set_heights does for host heights. Asynchronous; heights <= 0 or
+ * non-finite set the handle's status, which the next status query reports. */
+int mlswlbm_set_heights_device(mlsw_handle* h, const float* dev_in);
+
 /* Restarts from heights (host, [n][ny][nx]): f = f_eq(h, U = 0). The
  * values are checked on the device: a value <= 0 or non-finite is reported
  * as MLSW_ERR_NONFINITE by the next status query (mlswlbm_status,

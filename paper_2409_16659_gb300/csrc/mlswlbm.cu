@@ -512,6 +512,14 @@ int mlswlbm_set_heights(mlsw_handle* h, const float* h_in) {
   return MLSW_OK;
 }
 
+int mlswlbm_set_heights_device(mlsw_handle* h, const float* dev_in) {
+  if (!h || !dev_in) return MLSW_ERR_ARG;
+  CU(mlsw::launch_init(h->Q, h->p.n_layers, h->kp.L, h->p.lattice == MLSW_D2Q9, dev_in,
+                       h->f[h->cur], h->sh, h->status, h->stream));
+  h->launches += 1;
+  return MLSW_OK;
+}
+
 int mlswlbm_step(mlsw_handle* h, long nsteps) {
   if (!h || nsteps < 0) return MLSW_ERR_ARG;
   mlsw::StepLaunch a;

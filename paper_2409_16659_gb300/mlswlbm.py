@@ -81,6 +81,7 @@ EXPORTS = {
     "mlswlbm_step": (ctypes.c_int, [_H, ctypes.c_long]),
     "mlswlbm_get_heights": (ctypes.c_int, [_H, _F]),
     "mlswlbm_get_heights_device": (ctypes.c_int, [_H, ctypes.c_void_p]),
+    "mlswlbm_set_heights_device": (ctypes.c_int, [_H, ctypes.c_void_p]),
     "mlswlbm_set_heights": (ctypes.c_int, [_H, _F]),
     "mlswlbm_get_state": (ctypes.c_int, [_H, _F]),
     "mlswlbm_set_state": (ctypes.c_int, [_H, _F]),
@@ -276,6 +277,10 @@ class Solver:
         _check(lib().mlswlbm_get_heights_device(self._h, _dev_ptr(dev_out, self.n * self.ncell)),
                "mlswlbm_get_heights_device")
         return dev_out
+
+    def set_heights_device(self, dev_in):
+        _check(lib().mlswlbm_set_heights_device(self._h, _dev_ptr(dev_in, self.n * self.ncell)),
+               "mlswlbm_set_heights_device")
 
     def set_heights(self, h):
         a = _host_f32(h, self.n * self.ncell)

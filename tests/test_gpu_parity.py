@@ -343,6 +343,29 @@ def test_pinned_host_heights_match_pageable():
             b.get_heights(pin_out.numpy())
 
 
+def test_set_heights_from_device_memory_equals_host():
+    """mlswlbm_set_heights_device restarts the state exactly as the host
+    call does, and bad heights set the status."""
+    import torch
+    p = workloads.random_params(77, 3, B.MLSW_D2Q9, 72, 40)
+    h0 = workloads.random_heights(78, p).astype(np.float32)
+    with B.Solver(p, h0) as a, B.Solver(p, h0) as b:
+        a.step(9)
+        b.step(9)
+        h1 = workloads.random_heights(79, p).astype(np.float32)
+        a.set_heights(h1)
+        b.set_heights_device(torch.from_numpy(h1).cuda())
+        torch.cuda.synchronize()
+        assert np.array_equal(a.get_state(), b.get_state())
+        a.step(4)
+        b.step(4)
+        assert np.array_equal(a.get_heights(), b.get_heights())
+        bad = h1.copy()
+        bad[0, 1, 2] = 0.0
+        b.set_heights_device(torch.from_numpy(bad).cuda())
+        assert b.status() == B.MLSW_ERR_NONFINITE
+
+
 @pytest.mark.parametrize("n,nx,ny", [(3, 1024, 1024), (1, 1024, 1024), (5, 512, 400)])
 def test_large_pinned_read_out_matches_pageable(n, nx, ny):
     """Large page-locked outputs (up to 12.6 MB, one to five layers) are
