@@ -502,12 +502,15 @@ def surrogate_workload(B, torch):
                             "lbm_64_steps": 1e6 * (t4 - t3) / 20}
         tau = S.calibrate(etr, ctr)
         hr, taken, secs = S.rollout(s, params[60], heights[60], nwin, tau)
+        hh, taken_h, secs_h = S.rollout(s, params[60], heights[60], nwin, tau, hand_over=True)
         hl, secs_l = S.lbm_rollout(params[60], heights[60], nwin)
         hs = params[60]["hstar"]
         res["rollout"] = {"windows": nwin, "tau": tau, "surrogate_windows": taken,
                           "s": secs, "lbm_only_s": secs_l,
                           "surrogate_stats": S.film_statistics(hr, hs),
-                          "lbm_stats": S.film_statistics(hl, hs)}
+                          "lbm_stats": S.film_statistics(hl, hs),
+                          "hand_over": {"surrogate_windows": taken_h, "s": secs_h,
+                                        "stats": S.film_statistics(hh, hs)}}
     res["note"] = ("errors are the largest height difference per window of 64 steps; the "
                    "nonlinear windows start at step 5760, before rupture (~7200)")
     return res

@@ -103,12 +103,15 @@ def calibrate(err, change, bound=1e-3, quantile=1.0):
     return float(c[good[-1]]) if good.size else 0.0
 
 
-def rollout(s, params, h0, windows, tau):
+def rollout(s, params, h0, windows, tau, hand_over=False):
     """Advances one instance by `windows` windows: the surrogate's window is
     taken when its predicted largest change is at most tau, otherwise the LBM
     runs the 64 steps, restarted from the current heights (all on the
-    device; one host read of the predicted change per window). Returns
-    (heights, windows taken from the surrogate, seconds)."""
+    device; one host read of the predicted change per window). With
+    hand_over, the first window the surrogate does not take hands all the
+    remaining windows to the LBM in one call (a film whose change has grown
+    past tau keeps changing faster until it has dewetted). Returns (heights,
+    windows taken from the surrogate, seconds)."""
     torch = _torch()
     n, ny, nx = int(params["n"]), int(params["ny"]), int(params["nx"])
     h = torch.from_numpy(np.asarray(h0, dtype=np.float32).reshape(1, n, ny, nx)).cuda()
@@ -118,15 +121,17 @@ def rollout(s, params, h0, windows, tau):
                   stream=torch.cuda.current_stream()) as lbm:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(windows):
+        for w in range(windows):
             s.predict(h, pred)
             if float((pred - h).abs().amax()) <= tau:
                 h, pred = pred, h
                 taken += 1
             else:
                 lbm.set_heights_device(h[0])
-                lbm.step(WINDOW)
+                lbm.step(WINDOW * (windows - w if hand_over else 1))
                 lbm.get_heights_device(h[0])
+                if hand_over:
+                    break
         torch.cuda.synchronize()
         secs = time.perf_counter() - t0
         if lbm.status() != B.MLSW_OK:
