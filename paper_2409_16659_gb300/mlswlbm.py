@@ -618,7 +618,9 @@ class Surrogate:
         return int(_surr_lib().mlswlbm_surrogate_param_count())
 
     def _batch(self, t):
-        if not (t.is_cuda and t.dtype.__str__() == "torch.float32" and t.is_contiguous()):
+        import torch
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32
+                and t.is_contiguous()):
             raise ValueError("float32 contiguous CUDA tensor expected")
         if tuple(t.shape[1:]) != (self.n, self.ny, self.nx) or not 1 <= t.shape[0] <= self.max_batch:
             raise ValueError("shape [batch][n][ny][nx] expected")
