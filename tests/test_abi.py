@@ -155,3 +155,25 @@ def test_gpu_test_cases_pass_the_stability_check():
     for p, h in cases:
         rc, out = _create_rc(p, h)
         assert rc in (B.MLSW_OK, B.MLSW_ERR_CUDA), (rc, p)
+
+
+def test_surrogate_argument_checks_and_parameter_count():
+    """The surrogate's C entry points reject bad arguments before touching
+    the GPU; its parameter count is that of three 5 x 5 convolutions
+    16 -> 32 -> 32 -> 16 with biases."""
+    import ctypes
+    L = B.lib()
+    assert L.mlswlbm_surrogate_param_count() == 25 * (16 * 32 + 32 * 32 + 32 * 16) + 32 + 32 + 16
+    out = ctypes.c_void_p(1)
+    for args in [(0, 64, 64, 4), (6, 64, 64, 4), (2, 40, 64, 4), (2, 8, 64, 4), (2, 64, 0, 4),
+                 (2, 64, 64, 0)]:
+        rc = L.mlswlbm_surrogate_create(*args, 1, 10.0, 40.0, None, ctypes.byref(out))
+        assert rc == B.MLSW_ERR_ARG and not out.value, args
+        out = ctypes.c_void_p(1)
+    for scales in [(0.0, 40.0), (10.0, -1.0), (float("inf"), 40.0)]:
+        rc = L.mlswlbm_surrogate_create(2, 64, 64, 4, 1, *scales, None, ctypes.byref(out))
+        assert rc == B.MLSW_ERR_ARG, scales
+    assert L.mlswlbm_surrogate_create(2, 64, 64, 4, 1, 10.0, 40.0, None, None) == B.MLSW_ERR_ARG
+    assert L.mlswlbm_surrogate_predict(None, None, None, 1) == B.MLSW_ERR_ARG
+    assert L.mlswlbm_surrogate_train_step(None, None, None, 1, 1e-3, None) == B.MLSW_ERR_ARG
+    L.mlswlbm_surrogate_destroy(None)
