@@ -53,3 +53,25 @@ def test_fit_rejects_bad_arguments():
         B.fit_cap_angle([1.0], [1.0], 0.0)                  # one ring
     with pytest.raises(ValueError):
         B.fit_cap_angle([1.0, 0.5], [1.0], 0.0)
+
+
+def test_radial_profile_reference_exact_cases():
+    """The ring means that the device profiles are checked against: a
+    constant field is that constant in every ring, a field equal to floor(r)
+    around the centre (periodic distances) is b in ring b, and every cell
+    lies in exactly one ring."""
+    ny, nx = 24, 40
+    centre = (13.25, 7.5)
+    y, x = np.meshgrid(np.arange(ny, dtype=float), np.arange(nx, dtype=float), indexing="ij")
+    dx = x - centre[0]
+    dx -= nx * np.round(dx / nx)
+    dy = y - centre[1]
+    dy -= ny * np.round(dy / ny)
+    r = np.hypot(dx, dy)
+    nb = int(r.max()) + 1
+    rad, prof, area = droplets.radial_profile(np.full((ny, nx), 2.5), centre, nb)
+    assert np.all(prof[area > 0] == 2.5) and area.sum() == nx * ny
+    rad, prof, area = droplets.radial_profile(np.floor(r), centre, nb)
+    nz = area > 0
+    np.testing.assert_array_equal(prof[nz], np.arange(nb)[nz])
+    np.testing.assert_array_equal(rad, np.arange(nb) + 0.5)
