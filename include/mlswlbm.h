@@ -301,6 +301,20 @@ void mlswlbm_destroy(mlsw_handle* h);
 const char* mlswlbm_strerror(int code);
 
 /*
+ * Bounds-checked build. A library compiled with -DMLSW_DEBUG checks every
+ * padded-layout index, every shared-memory access and global store of the
+ * step kernels and the coordinates of every tile copy; an access out of
+ * range is counted and sent to a padding cell instead of faulting, so the
+ * results are wrong but the GPU is not. This call synchronises the device,
+ * returns in *count the accesses out of range since the previous call and
+ * clears the counters. It checks the implementation, not a passage of the
+ * paper.
+ * Errors: MLSW_ERR_ARG (count NULL), MLSW_ERR_CUDA (the counters could not be
+ * read), MLSW_ERR_UNSUPPORTED (a release build: *count = 0).
+ */
+int mlswlbm_debug_bounds_violations(unsigned long long* count);
+
+/*
  * Per-cell friction 2 mu_i h_i a_i (Eq. friction_force) for ncell
  * independent cells, on the device. h, Jx, Jy, Rx, Ry: device pointers of
  * n*ncell floats, layout [i][cell]; Jy/Ry may be NULL (one component).
@@ -333,9 +347,11 @@ int mlswlbm_friction_eval(const mlsw_params* p, long ncell, const float* h,
  * block is used per 16384 cells, so lattices above 4096 * 16384 cells
  * (67,108,864) return MLSW_ERR_UNSUPPORTED. The first call on a device looks
  * up the array's device address (with that device current) and should come
- * before any stream capture. Every call shares the array and overwrites
- * the partials it uses; calls that overlap on the GPU race on it. Calls no
- * cudaMalloc, cudaFree or other allocating routine.
+ * before any stream capture; only a successful look-up is kept, so after a
+ * failed one (MLSW_ERR_CUDA) the next call on that device tries again.
+ * Every call shares the array and overwrites the partials it uses; calls
+ * that overlap on the GPU race on it. Calls no cudaMalloc, cudaFree or other
+ * allocating routine.
  * Errors: MLSW_ERR_ARG (NULL pointer, invalid p, non-finite H),
  * MLSW_ERR_UNSUPPORTED (lattice beyond the scratch, device ordinal >= 64),
  * MLSW_ERR_CUDA (symbol look-up or launch failed).

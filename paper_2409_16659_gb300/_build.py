@@ -2,7 +2,9 @@
 
 Each translation unit is compiled in parallel, then linked into one shared
 library with the CUDA runtime linked statically (no dependency on the
-runtime PyTorch ships).
+runtime PyTorch ships). build(debug=True) makes the bounds-checked variant
+libmlswlbm_debug.so (-DMLSW_DEBUG, objects in _lib/debug/), which the tests
+build on demand.
 """
 import concurrent.futures as cf
 import os
@@ -14,6 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libmlswlbm.so")
+DEBUG_LIB = os.path.join(OUT_DIR, "libmlswlbm_debug.so")
 SOURCES = ["mlswlbm.cu", "step_kernels.cu", "aux_kernels.cu", "noalloc.cu", "batch.cu",
            "analysis.cu", "surrogate.cu"]
 HEADERS = ["physics.cuh", "kernels.h", "tma.cuh", "host.h"]
@@ -30,15 +33,15 @@ def _deps():
     return files
 
 
-def _stale():
-    if not os.path.exists(LIB):
+def _stale(lib):
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(f) > t for f in _deps())
 
 
-def _compile(src, extra):
-    obj = os.path.join(OUT_DIR, os.path.splitext(src)[0] + ".o")
+def _compile(src, extra, obj_dir=OUT_DIR):
+    obj = os.path.join(obj_dir, os.path.splitext(src)[0] + ".o")
     cmd = [NVCC, *ARCH, *CFLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -46,24 +49,28 @@ def _compile(src, extra):
     return obj, r.stderr
 
 
-def build(force=False, verbose=False, extra=()):
-    """Compiles the library if a source changed; returns its path."""
-    if not force and not _stale():
-        return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force=False, verbose=False, extra=(), debug=False):
+    """Compiles the library (the bounds-checked one with debug=True) if a
+    source changed; returns its path."""
+    lib = DEBUG_LIB if debug else LIB
+    if not force and not _stale(lib):
+        return lib
+    obj_dir = os.path.join(OUT_DIR, "debug") if debug else OUT_DIR
+    os.makedirs(obj_dir, exist_ok=True)
+    flags = list(extra) + (["-DMLSW_DEBUG"] if debug else [])
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        results = list(ex.map(lambda s: _compile(s, list(extra)), SOURCES))
+        results = list(ex.map(lambda s: _compile(s, flags, obj_dir), SOURCES))
     if verbose:
         for _, err in results:
             if err:
                 sys.stderr.write(err)
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = lib + ".tmp%d" % os.getpid()
     cmd = [NVCC, *ARCH, "-shared", "-o", tmp] + [o for o, _ in results]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("nvcc link failed:\n%s%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

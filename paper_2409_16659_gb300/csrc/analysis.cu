@@ -225,4 +225,6 @@ cudaError_t launch_radial_profile(int Q, int n, const Layout& L, const float* f,
   return cudaGetLastError();
 }
 
+MLSW_DEFINE_BOUNDS_READER(bounds_violations_analysis)
+
 }  // namespace mlsw

@@ -651,4 +651,6 @@ cudaError_t launch_wait_selftest(int arrive, unsigned limit, int* status, cudaSt
   return cudaGetLastError();
 }
 
+MLSW_DEFINE_BOUNDS_READER(bounds_violations_aux)
+
 }  // namespace mlsw

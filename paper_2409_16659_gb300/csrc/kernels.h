@@ -29,6 +29,7 @@ struct StepLaunch {
   int* status;
   int* sched;                   // D2Q9: two zero-initialised tile-scheduler counters
   int num_sms;
+  int reverse;                  // D2Q9: 1 = tiles in reverse order (see SingleTiles)
 };
 cudaError_t launch_step(const StepLaunch& a, cudaStream_t st);
 
@@ -176,7 +177,7 @@ cudaError_t launch_friction_eval(const KParams& P, long ncell, const float* h, c
 cudaError_t launch_wait_selftest(int arrive, unsigned limit, int* status, cudaStream_t st);
 
 // Dense layout of a caller-owned population array (no ghosts).
-inline Layout dense_layout(int nx, int ny) {
+inline Layout dense_layout(int nx, int ny, int nplanes = 0) {
   Layout L;
   L.nx = nx;
   L.ny = ny;
@@ -185,7 +186,15 @@ inline Layout dense_layout(int nx, int ny) {
   L.pitch = nx;
   L.rows = ny;
   L.plane = (long)nx * ny;
+  L.nplanes = nplanes;
   return L;
 }
+
+// Bounds-checked build: accesses out of range since the last call, per
+// translation unit with device code (0 in release builds; ~0u if the
+// counter could not be read).
+unsigned bounds_violations_step();
+unsigned bounds_violations_aux();
+unsigned bounds_violations_analysis();
 
 }  // namespace mlsw

@@ -175,6 +175,7 @@ mlsw::Layout make_layout(const mlsw_params& p) {
   L.pitch = round_up(p.nx, tx) + 8;
   L.rows = (p.lattice == MLSW_D2Q9) ? round_up(p.ny, ty) + 4 : 1;
   L.plane = (long)L.pitch * L.rows;
+  L.nplanes = p.n_layers * Qof(p.lattice);
   return L;
 }
 
@@ -447,6 +448,13 @@ int mlswlbm_create(const mlsw_params* p, const float* h_init, void* stream, mlsw
   }
   h->num_sms = sms > 0 ? sms : 1;
   h->nblk_diag = 2 * h->num_sms;
+  {
+    // a buffer that fits in 90 % of the L2 is kept there between steps
+    int l2 = 0;
+    if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess) l2 = 0;
+    const double buf = (double)h->flen * sizeof(float);
+    h->kp.l2_policy = (l2 > 0 && buf <= 0.9 * l2) ? mlsw::kL2Resident : mlsw::kL2Stream;
+  }
   if (!(p->flags & MLSW_FLAG_NO_PERSISTENT)) {
     int optin = 0;
     const size_t need = mlsw::step_persistent_smem(n, p->lattice, p->nx);
@@ -528,6 +536,7 @@ int mlswlbm_step(mlsw_handle* h, long nsteps) {
   a.status = h->status;
   a.sched = h->status + 1;
   a.num_sms = h->num_sms;
+  a.reverse = 0;
   if (h->psmem) {
     // whole lattice in one CTA: chunks of steps per launch
     constexpr long kChunk = 16384;
@@ -546,6 +555,11 @@ int mlswlbm_step(mlsw_handle* h, long nsteps) {
     a.fin = h->f[h->cur];
     a.fout = h->f[h->cur ^ 1];
     a.fin_map = &h->map[h->cur];
+    // unless a whole buffer stays in the L2, steps from buffer 1 run their
+    // tiles in reverse order: every step then begins with the rows its
+    // predecessor wrote last, which the L2 still holds (the results do not
+    // depend on the order)
+    a.reverse = h->kp.l2_policy == mlsw::kL2Stream ? h->cur : 0;
     CU(mlsw::launch_step(a, h->stream));
     h->launches += 1;
     if (h->kp.tiny) {
@@ -876,6 +890,25 @@ int mlswlbm_selftest_bounded_wait(int arrive, unsigned limit, void* stream) {
   cudaFree(d);
   if (!ok) return MLSW_ERR_CUDA;
   return (flag & mlsw::kStatusTimeout) ? MLSW_ERR_TIMEOUT : MLSW_OK;
+}
+
+int mlswlbm_debug_bounds_violations(unsigned long long* count) {
+  if (!count) return MLSW_ERR_ARG;
+#ifdef MLSW_DEBUG
+  if (cudaDeviceSynchronize() != cudaSuccess) return MLSW_ERR_CUDA;
+  const unsigned parts[3] = {mlsw::bounds_violations_step(), mlsw::bounds_violations_aux(),
+                             mlsw::bounds_violations_analysis()};
+  unsigned long long total = 0;
+  for (unsigned v : parts) {
+    if (v == ~0u) return MLSW_ERR_CUDA;
+    total += v;
+  }
+  *count = total;
+  return MLSW_OK;
+#else
+  *count = 0;
+  return MLSW_ERR_UNSUPPORTED;
+#endif
 }
 
 int mlswlbm_set_stream(mlsw_handle* h, void* stream) {

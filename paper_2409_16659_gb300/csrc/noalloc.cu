@@ -26,17 +26,28 @@ constexpr int kNoallocMaxDevices = 64;
 
 static __device__ __align__(256) double g_diag_scratch[kNoallocBlocks * (MLSW_MAX_LAYERS + 2)];
 
-std::once_flag g_once[kNoallocMaxDevices];
-cudaError_t g_setup_err[kNoallocMaxDevices];
+std::mutex g_setup_mutex[kNoallocMaxDevices];
+bool g_ready[kNoallocMaxDevices];  // set only after a successful look-up
 double* g_scratch_ptr[kNoallocMaxDevices];
 
 // The host-side name g_diag_scratch is only a stand-in for the device
-// array; its device address is looked up once per device, with that device
-// current, and passed to the kernels.
-void setup_device(int dev) {
-  void* ptr = nullptr;
-  g_setup_err[dev] = cudaGetSymbolAddress(&ptr, g_diag_scratch);
-  g_scratch_ptr[dev] = (g_setup_err[dev] == cudaSuccess) ? static_cast<double*>(ptr) : nullptr;
+// array; its device address is looked up per device, with that device
+// current, and passed to the kernels. Only a successful look-up is kept: a
+// failed one returns the error and is tried again on the next call.
+cudaError_t scratch_of_device(int dev, double** out) {
+  std::lock_guard<std::mutex> lock(g_setup_mutex[dev]);
+  if (!g_ready[dev]) {
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_diag_scratch);
+    if (e != cudaSuccess || !ptr) {
+      (void)cudaGetLastError();  // leave no sticky error behind for the caller
+      return e != cudaSuccess ? e : cudaErrorInvalidSymbol;
+    }
+    g_scratch_ptr[dev] = static_cast<double*>(ptr);
+    g_ready[dev] = true;
+  }
+  *out = g_scratch_ptr[dev];
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -57,11 +68,11 @@ extern "C" int mlswlbm_diagnostics_noalloc(const mlsw_params* p, const float* f,
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return MLSW_ERR_CUDA;
   if (dev < 0 || dev >= kNoallocMaxDevices) return MLSW_ERR_UNSUPPORTED;
-  std::call_once(g_once[dev], setup_device, dev);
-  if (g_setup_err[dev] != cudaSuccess || !g_scratch_ptr[dev]) return MLSW_ERR_CUDA;
+  double* scratch = nullptr;
+  if (scratch_of_device(dev, &scratch) != cudaSuccess) return MLSW_ERR_CUDA;
   // every block writes its own partials, so nothing needs clearing first
   const cudaError_t e =
-      mlsw::launch_diagnostics(p->lattice, n, mlsw::dense_layout(p->nx, p->ny), f, sh,
-                               g_scratch_ptr[dev], (int)nblk, out, (cudaStream_t)stream);
+      mlsw::launch_diagnostics(p->lattice, n, mlsw::dense_layout(p->nx, p->ny, n * (p->lattice == MLSW_D1Q3 ? 3 : 9)), f, sh,
+                               scratch, (int)nblk, out, (cudaStream_t)stream);
   return e == cudaSuccess ? MLSW_OK : MLSW_ERR_CUDA;
 }

@@ -10,6 +10,31 @@ namespace mlsw {
 
 constexpr int kMaxLayers = 5;
 
+// ---------------------------------------------------------------------------
+// Bounds-checked build (compiled with -DMLSW_DEBUG). Index helpers check
+// every padded-layout index, shared-memory access and global store of the
+// step kernels; an access out of range is counted and redirected to a
+// harmless cell (index 0 of a population buffer is the padding cell
+// x = -4 of the first row, which no real cell reads) instead of faulting.
+// Each translation unit keeps its own counter; the host reads and clears
+// them through mlswlbm_debug_bounds_violations. Release builds compile
+// none of this.
+// ---------------------------------------------------------------------------
+#ifdef MLSW_DEBUG
+static __device__ unsigned int g_bounds_violations;
+__device__ __forceinline__ void note_bounds_violation() { atomicAdd(&g_bounds_violations, 1u); }
+#define MLSW_DEFINE_BOUNDS_READER(fn)                                                  \
+  unsigned fn() {                                                                      \
+    unsigned v = 0, z = 0;                                                             \
+    if (cudaMemcpyFromSymbol(&v, g_bounds_violations, sizeof v) != cudaSuccess) return ~0u; \
+    if (cudaMemcpyToSymbol(g_bounds_violations, &z, sizeof z) != cudaSuccess) return ~0u;   \
+    return v;                                                                          \
+  }
+#else
+#define MLSW_DEFINE_BOUNDS_READER(fn) \
+  unsigned fn() { return 0; }
+#endif
+
 // Kernel-side copy of the problem statement, rounded to FP32 once.
 //
 // Shifted rest population: the device stores g_0 = f_0 - H_i for the rest
@@ -35,9 +60,19 @@ struct Layout {
   int pitch;     // floats per padded row (multiple of 4)
   int rows;      // padded rows per plane
   long plane;    // pitch * rows
+  int nplanes;   // planes of a buffer (0: not known, planes are then not checked)
   __host__ __device__ long at(int p, int x, int y) const {
+#if defined(MLSW_DEBUG) && defined(__CUDA_ARCH__)
+    if (x + gx < 0 || x + gx >= pitch || y + gy < 0 || y + gy >= rows || p < 0 ||
+        (nplanes > 0 && p >= nplanes)) {
+      note_bounds_violation();
+      return 0;
+    }
+#endif
     return (long)p * plane + (long)(y + gy) * pitch + (x + gx);
   }
+  // floats of one buffer (0 when the plane count is not known)
+  __host__ __device__ long length() const { return (long)nplanes * plane; }
 };
 
 struct KParams {
@@ -71,7 +106,15 @@ struct KParams {
   // phi_k(d) = 2 a - a^2, a = e^{-kappa (d - k h*)}
   int wet_kind;
   float kappa;
+  // L2 cache policy of the D2Q9 step (see d2q9_tile_loop): kL2None,
+  // kL2Stream or kL2Resident
+  int l2_policy;
 };
+
+// kL2None: no cache hints (batches, whose many lattices stream through);
+// kL2Stream: a lattice larger than the L2, output kept as long as possible;
+// kL2Resident: one population buffer fits in the L2 and stays there.
+enum L2Policy { kL2None = 0, kL2Stream = 1, kL2Resident = 2 };
 
 // Substrate height at lattice cell (x, y) (any integers: the cosine is
 // periodic); the phase is reduced exactly in integers.

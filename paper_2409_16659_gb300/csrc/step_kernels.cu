@@ -34,6 +34,53 @@
 namespace mlsw {
 
 // ---------------------------------------------------------------------------
+// Bounds checks of the debug build (physics.cuh): a shared-memory pointer
+// must lie in the CTA's dynamic shared memory, an index in its array, a
+// global store in its buffer or plane. Out of range, the access is counted
+// and goes to the first element instead. Release builds pass through.
+// ---------------------------------------------------------------------------
+#ifdef MLSW_DEBUG
+extern __shared__ __align__(128) unsigned char dyn_smem_base[];
+__device__ __forceinline__ bool dyn_smem_ok(const void* p, int bytes) {
+  if (!__isShared(p)) return false;
+  uint32_t size;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(size));
+  const uint32_t a = smem_addr(p), lo = smem_addr(dyn_smem_base);
+  return a >= lo && a + (uint32_t)bytes <= lo + size;
+}
+#endif
+template <class P>
+__device__ __forceinline__ P* chk_smem(P* p) {
+#ifdef MLSW_DEBUG
+  if (!dyn_smem_ok(p, (int)sizeof(P))) {
+    note_bounds_violation();
+    return reinterpret_cast<P*>(dyn_smem_base);
+  }
+#endif
+  return p;
+}
+__device__ __forceinline__ int chk_index(int i, int n) {
+#ifdef MLSW_DEBUG
+  if (i < 0 || i >= n) {
+    note_bounds_violation();
+    return 0;
+  }
+#endif
+  return i;
+}
+// global store target: p inside [base, base + len)
+__device__ __forceinline__ float* chk_global(float* base, float* p, long len) {
+#ifdef MLSW_DEBUG
+  const long i = p - base;
+  if (i < 0 || i >= len) {
+    note_bounds_violation();
+    return base;
+  }
+#endif
+  return p;
+}
+
+// ---------------------------------------------------------------------------
 // Stores of one post-collision population to its streamed destination
 // (dx, dy) (already periodic) and to the ghost cells that image it.
 // ---------------------------------------------------------------------------
@@ -49,22 +96,45 @@ __device__ __forceinline__ int image_of(int d, int n) {
 __device__ __forceinline__ void store_edge(float* __restrict__ plane_base, const Layout& L,
                                            int dx, int dy, int xi, int yi, float v) {
   const long r0 = (long)(dy + L.gy) * L.pitch;
-  plane_base[r0 + dx + L.gx] = v;
-  if (xi != kNoImage) plane_base[r0 + xi + L.gx] = v;
+  *chk_global(plane_base, plane_base + r0 + dx + L.gx, L.plane) = v;
+  if (xi != kNoImage) *chk_global(plane_base, plane_base + r0 + xi + L.gx, L.plane) = v;
   if (yi != kNoImage) {
     const long r1 = (long)(yi + L.gy) * L.pitch;
-    plane_base[r1 + dx + L.gx] = v;
-    if (xi != kNoImage) plane_base[r1 + xi + L.gx] = v;
+    *chk_global(plane_base, plane_base + r1 + dx + L.gx, L.plane) = v;
+    if (xi != kNoImage) *chk_global(plane_base, plane_base + r1 + xi + L.gx, L.plane) = v;
   }
+}
+
+// ---------------------------------------------------------------------------
+// The rest population after the collision, g0* = g0 + delta: the stored rest
+// population g0 (shifted by H, O(h - H)) plus a small change (the incoming
+// moving populations less the outgoing equilibria, times omega when tau !=
+// 1). Rounding g0 + delta to FP32 loses up to half an ulp of g0 per cell
+// and step, and in a slowly changing film (a dewetted precursor far from H)
+// that loss has the same sign step after step. The exact rounding error
+// (Fast2Sum, |g0| >= |delta| in the cells where it matters) is passed on
+// instead, half to each of two opposite moving populations: their ulp is
+// orders of magnitude finer, the momentum they carry is unchanged, and the
+// cell's populations sum to the incoming mass to their rounding.
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ T rest_update(T g0, T delta, T& fa, T& fb) {
+  const T out = g0 + delta;
+  const T r = delta - (out - g0);  // exact: the part of delta the sum dropped
+  fa = fmav(r, 0.5f, fa);
+  fb = fmav(r, 0.5f, fb);
+  return out;
 }
 
 // Equilibrium, BGK with forcing for one layer at one cell; fs[k] receives
 // the post-collision populations (rest one stored shifted by H).
-// f_old (read only when !TAU1) holds the stored pre-collision populations.
+// g0: the stored rest population; small: the sum of the stored moving ones
+// (h - H = g0 + small); f_old (read only when !TAU1) holds the stored
+// pre-collision populations.
 template <int LAT, bool TAU1>
-__device__ __forceinline__ void collide(const KParams& P, float h, float dh, float jx, float jy,
-                                        float Fx, float Fy, const float* f_old,
-                                        float (&fs)[Lattice<LAT>::Q]) {
+__device__ __forceinline__ void collide(const KParams& P, float h, float g0, float small,
+                                        float jx, float jy, float Fx, float Fy,
+                                        const float* f_old, float (&fs)[Lattice<LAT>::Q]) {
   using Lt = Lattice<LAT>;
   const float inv_h = rcp(h);
   const float ux = jx * inv_h, uy = jy * inv_h;
@@ -82,9 +152,10 @@ __device__ __forceinline__ void collide(const KParams& P, float h, float dh, flo
   }
   // rest population: h - sum of the moving equilibria, which equals
   // h (1 - w_0 U^2 / (2 cs^2)) and keeps the cell's mass exact in the sum;
-  // stored shifted by H, i.e. dh - sum_eq
-  const float geq0 = dh - sum_eq;
-  fs[0] = TAU1 ? geq0 : f_old[0] + P.omega * (geq0 - f_old[0]);
+  // stored shifted by H: g0 + (small - sum_eq), relaxed by omega when
+  // tau != 1 (the moving populations then keep 1 - omega of small)
+  const float d = small - sum_eq;
+  fs[0] = rest_update(g0, TAU1 ? d : P.omega * d, fs[1], fs[2]);
 }
 
 // ---------------------------------------------------------------------------
@@ -95,8 +166,8 @@ __device__ __forceinline__ void collide(const KParams& P, float h, float dh, flo
 // 3 (0,1), 4 (-1,1); 5..8 are their opposites.
 // ---------------------------------------------------------------------------
 template <bool TAU1, class T>
-__device__ __forceinline__ void collide_d2q9(const KParams& P, T h, T dh, T jx, T jy, T Fx, T Fy,
-                                             const T* f_old, T (&fs)[9]) {
+__device__ __forceinline__ void collide_d2q9(const KParams& P, T h, T g0, T small, T jx, T jy,
+                                             T Fx, T Fy, const T* f_old, T (&fs)[9]) {
   const T ih = rcp(h);
   const T ux = jx * ih, uy = jy * ih;
   const T u15 = 1.5f * fmav(ux, ux, uy * uy);
@@ -121,12 +192,20 @@ __device__ __forceinline__ void collide_d2q9(const KParams& P, T h, T dh, T jx, 
     }
   }
   // rest population h - (sum of moving equilibria) = h (1 - w_0 U^2/(2 cs^2)),
-  // stored shifted by H
-  const T geq0 = fmav(-2.f, sumsym, dh);
-  if constexpr (TAU1)
-    fs[0] = geq0;
-  else
-    fs[0] = fmav(P.omega, geq0 - f_old[0], f_old[0]);
+  // stored shifted by H: g0 + (small - 2 sumsym), relaxed by omega when
+  // tau != 1 (see rest_update)
+  const T d = fmav(-2.f, sumsym, small);
+  fs[0] = rest_update(g0, TAU1 ? d : P.omega * d, fs[1], fs[5]);
+}
+
+// Sum of the eight stored moving populations of one layer at a cell: the
+// opposite directions first (their moving parts nearly cancel), then the
+// diagonals with the axes. The layer's h - H is the rest population plus
+// this sum, added last: adding the small populations to the O(h - H) rest
+// population one by one would drop their low bits one direction at a time.
+template <class T>
+__device__ __forceinline__ T moving_sum(const T (&v)[9]) {
+  return ((v[1] + v[5]) + (v[3] + v[7])) + ((v[2] + v[6]) + (v[4] + v[8]));
 }
 
 // Loads / stores of one cell (float) or of a pair of cells (f2) at two
@@ -134,17 +213,17 @@ __device__ __forceinline__ void collide_d2q9(const KParams& P, T h, T dh, T jx, 
 template <class T> struct Lanes;
 template <> struct Lanes<float> {
   static constexpr int W = 1;
-  __device__ static float ld(const float* a, const float*) { return *a; }
-  __device__ static void st(float* a, float*, float v) { *a = v; }
+  __device__ static float ld(const float* a, const float*) { return *chk_smem(a); }
+  __device__ static void st(float* a, float*, float v) { *chk_smem(a) = v; }
   __device__ static float get(float v, int) { return v; }
   __device__ static float ld2(float a, float) { return a; }
 };
 template <> struct Lanes<f2> {
   static constexpr int W = 2;
-  __device__ static f2 ld(const float* a, const float* b) { return mk2(*a, *b); }
+  __device__ static f2 ld(const float* a, const float* b) { return mk2(*chk_smem(a), *chk_smem(b)); }
   __device__ static void st(float* a, float* b, f2 v) {
-    *a = v.v.x;
-    *b = v.v.y;
+    *chk_smem(a) = v.v.x;
+    *chk_smem(b) = v.v.y;
   }
   __device__ static float get(f2 v, int l) { return l ? v.v.y : v.v.x; }
   __device__ static f2 ld2(float a, float b) { return mk2(a, b); }
@@ -202,13 +281,19 @@ struct TileRef {
   int bx, by;
 };
 
-// Tiles of one lattice (the single-solver kernel).
+// Tiles of one lattice (the single-solver kernel). Tile t of a step runs
+// in row-major order, or in reverse order when rev is set: the solver
+// alternates the two, so that each step starts on the rows the previous
+// step wrote last, which are still in the L2.
 struct SingleTiles {
   const KParams* P;
   const CUtensorMap* map;
   float* fout;
-  int ntx, ntiles;
-  __device__ TileRef operator()(int t) const { return {P, map, fout, t % ntx, t / ntx}; }
+  int ntx, ntiles, rev;
+  __device__ TileRef operator()(int t) const {
+    const int u = rev ? ntiles - 1 - t : t;
+    return {P, map, fout, u % ntx, u / ntx};
+  }
   __device__ void prefetch() const { tma_prefetch_desc(map); }
 };
 
@@ -250,12 +335,36 @@ __device__ __forceinline__ void d2q9_tile_loop(const Tiles& tiles, int* __restri
   const int tid = threadIdx.x;
   const int ntiles = tiles.ntiles;
 
+  // L2 policies (KParams::l2_policy). For a single lattice the step's
+  // output is written evict_last, so that as much of it as the L2 holds is
+  // still there when the next step reads it. When a whole buffer fits
+  // (kL2Resident), the input is read evict_first: it is dead once read, and
+  // the output lines keep the L2. A larger lattice (kL2Stream) reads with
+  // the lines' priority unchanged (halo rows are read again by the tile row
+  // below) and the solver alternates the tile order, so each step starts on
+  // the rows its predecessor wrote last. Batches (kL2None) use no hints:
+  // kept output lines would only crowd out the halo rows of other tiles.
+  const int l2pol = tiles(blockIdx.x).P->l2_policy;  // grid <= ntiles
+  const uint64_t st_pol = l2pol == kL2None ? pol_evict_normal() : pol_evict_last();
+  const uint64_t ld_pol = l2pol == kL2Resident ? pol_evict_first()
+                          : (l2pol == kL2Stream ? pol_evict_unchanged() : pol_evict_normal());
   auto issue = [&](int t) {
     const TileRef r = tiles(t);
     fence_proxy_async_smem();
+#ifdef MLSW_DEBUG
+    // the box must start on a 16-byte boundary and lie inside the padded
+    // planes; a bad box is not copied (the barrier completes without data)
+    const Layout& L = r.P->L;
+    if ((r.bx * TX) % 4 != 0 || r.bx * TX + BW > L.pitch || r.by * TY + BH > L.rows ||
+        (long)BH * BW * Tl::PN * 4 != (long)Tl::kStageBytes) {
+      note_bounds_violation();
+      mbar_arrive_expect_tx(bar, 0u);  // the one arrival, no bytes
+      return;
+    }
+#endif
     mbar_arrive_expect_tx(bar, (uint32_t)Tl::kStageBytes);
     // box origin: real (x0 - 4, y0 - 2) = padded (x0, y0) since gx = 4, gy = 2
-    tma_load_3d(stage, r.map, bar, r.bx * TX, r.by * TY, 0);
+    tma_load_3d(stage, r.map, bar, r.bx * TX, r.by * TY, 0, ld_pol);
   };
   auto draw_next = [&]() {
     const int nt = (int)gridDim.x + atomicAdd(sched, 1);
@@ -283,6 +392,14 @@ __device__ __forceinline__ void d2q9_tile_loop(const Tiles& tiles, int* __restri
     mbar_init(bar, 1);
     mbar_init_fence();
   }
+  // Programmatic dependent launch: the next step's grid may be scheduled
+  // while this one drains, and this grid's set-up above overlaps the
+  // previous step's tail. Every global access (the tile loads, the stores
+  // into the previous step's input buffer, the counters) comes after the
+  // wait for the previous grid's completion. Both are no-ops in a launch
+  // without the programmatic attribute.
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   __syncthreads();
   if (tid == 0) {
     tiles.prefetch();
@@ -310,6 +427,11 @@ __device__ __forceinline__ void d2q9_tile_loop(const Tiles& tiles, int* __restri
     auto z0_at = [&](int c, int r) { return substrate_at(P, x0 + c, y0 + r); };
 
     // ---- M. moments: deviations z on the two-ring region, J on the tile ----
+    // A tile cell's rest population g0 and the sum of its moving ones stay
+    // in registers for the collision (h - H = g0 + small): recovering
+    // h - H as z_i - z_{i-1} would round it to the resolution of z_i, and
+    // that rounding is not mass-neutral.
+    T g0s[N], sms[N];
     {
       const int rA = iyb + 2, rB = iyb + (W - 1) * BY + 2, c = ix + 2;  // two-ring coords
       const float* sA = stage + rA * BW + (c + 2);  // stage column = c + 2
@@ -321,7 +443,9 @@ __device__ __forceinline__ void d2q9_tile_loop(const Tiles& tiles, int* __restri
         T v[Q];
 #pragma unroll
         for (int k = 0; k < Q; ++k) v[k] = Ln::ld(sA + (i * Q + k) * BH * BW, sB + (i * Q + k) * BH * BW);
-        z += ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
+        g0s[i] = v[0];
+        sms[i] = moving_sum(v);
+        z += g0s[i] + sms[i];
         Ln::st(zs + (i * RH + rA) * RW + c, zs + (i * RH + rB) * RW + c, z);
         Ln::st(js + ((0 * N + i) * TY + rA - 2) * TX + ix, js + ((0 * N + i) * TY + rB - 2) * TX + ix,
                ((v[1] + v[2]) + v[8]) - ((v[4] + v[5]) + v[6]));
@@ -348,7 +472,7 @@ __device__ __forceinline__ void d2q9_tile_loop(const Tiles& tiles, int* __restri
 #pragma unroll
         for (int k = 0; k < Q; ++k)
           v[k] = Ln::ld(srcA + (i * Q + k) * BH * BW, srcB + (i * Q + k) * BH * BW);
-        z += ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
+        z += v[0] + moving_sum(v);
         Ln::st(zs + (i * RH + rA) * RW + cA, zs + (i * RH + rB) * RW + cB, z);
       }
     }
@@ -449,17 +573,11 @@ __device__ __forceinline__ void d2q9_tile_loop(const Tiles& tiles, int* __restri
 #pragma unroll
       for (int l = 0; l < W; ++l) valid[l] = gx < nx && y0 + iyb + l * BY < ny;
       if (valid[0]) {  // lane 0 invalid implies lane 1 invalid
-        T hh[N], dd[N], jx[N], jy[N];
+        T hh[N], jx[N], jy[N];
         {
-          T zprev = Num<T>::splat(0.f);
-          if (sub) zprev = Ln::ld2(z0_at(ix, iyA), z0_at(ix, iyB));
 #pragma unroll
           for (int i = 0; i < N; ++i) {
-            const T zi = Ln::ld(zs + (i * RH + iyA + 2) * RW + ix + 2,
-                                zs + (i * RH + iyB + 2) * RW + ix + 2);
-            dd[i] = zi - zprev;
-            zprev = zi;
-            hh[i] = dd[i] + P.H[i];
+            hh[i] = (g0s[i] + sms[i]) + P.H[i];
             jx[i] = Ln::ld(js + ((0 * N + i) * TY + iyA) * TX + ix, js + ((0 * N + i) * TY + iyB) * TX + ix);
             jy[i] = Ln::ld(js + ((1 * N + i) * TY + iyA) * TX + ix, js + ((1 * N + i) * TY + iyB) * TX + ix);
           }
@@ -527,14 +645,17 @@ __device__ __forceinline__ void d2q9_tile_loop(const Tiles& tiles, int* __restri
             for (int k = 0; k < Q; ++k) fo[k] = Ln::ld(sA + (i * Q + k) * BH * BW, sB + (i * Q + k) * BH * BW);
           }
           T fs[Q];
-          collide_d2q9<TAU1>(P, h, dd[i], jx[i], jy[i], Fx, Fy, fo, fs);
+          collide_d2q9<TAU1>(P, h, g0s[i], sms[i], jx[i], jy[i], Fx, Fy, fo, fs);
           if (inner) {
 #pragma unroll
             for (int l = 0; l < W; ++l) {
 #pragma unroll
               for (int k = 0; k < Q; ++k)
-                cbase[l][(long)i * lplane + (long)k * L.plane +
-                         Lattice<2>::cy(k) * L.pitch + Lattice<2>::cx(k)] = Ln::get(fs[k], l);
+                st_global_hint(chk_global(fout,
+                                          &cbase[l][(long)i * lplane + (long)k * L.plane +
+                                                    Lattice<2>::cy(k) * L.pitch + Lattice<2>::cx(k)],
+                                          L.length()),
+                               Ln::get(fs[k], l), st_pol);
             }
             continue;
           }
@@ -544,7 +665,8 @@ __device__ __forceinline__ void d2q9_tile_loop(const Tiles& tiles, int* __restri
             if (!valid[l]) continue;
             if (!images[l]) {
 #pragma unroll
-              for (int k = 0; k < Q; ++k) obase[koff[l][k]] = Ln::get(fs[k], l);
+              for (int k = 0; k < Q; ++k)
+                *chk_global(fout, obase + koff[l][k], L.length()) = Ln::get(fs[k], l);
             } else {
 #pragma unroll
               for (int k = 0; k < Q; ++k) {
@@ -576,10 +698,10 @@ template <int N, int MODE>
 __global__ void __launch_bounds__(256, 2)
     step_d2q9_tma(const __grid_constant__ CUtensorMap fin_map, float* __restrict__ fout,
                   const __grid_constant__ KParams P, int* __restrict__ status,
-                  int* __restrict__ sched) {
+                  int* __restrict__ sched, int rev) {
   using Tl = D2Tile<N>;
   const int ntx = (P.nx + Tl::TX - 1) / Tl::TX, nty = (P.ny + Tl::TY - 1) / Tl::TY;
-  const SingleTiles tiles{&P, &fin_map, fout, ntx, ntx * nty};
+  const SingleTiles tiles{&P, &fin_map, fout, ntx, ntx * nty, rev};
   d2q9_tile_loop<N, MODE, Tl::RPT>(tiles, status, sched);
 }
 
@@ -625,7 +747,8 @@ __device__ __forceinline__ void d1q3_pressures(const KParams& P, const float (&z
 // post-collision populations; f_old is read only when !TAU1. Returns true
 // when a height is not positive or a force not finite.
 template <int N, bool TAU1>
-__device__ __forceinline__ bool d1q3_collide_cell(const KParams& P, const float (&dd)[N],
+__device__ __forceinline__ bool d1q3_collide_cell(const KParams& P, const float (&g0)[N],
+                                                  const float (&sm)[N],
                                                   const float (&hh)[N], const float (&jx)[N],
                                                   const float (&pw)[N], const float (&pc)[N],
                                                   const float (&pe)[N], const float (&f_old)[N][3],
@@ -641,7 +764,7 @@ __device__ __forceinline__ bool d1q3_collide_cell(const KParams& P, const float 
     const float h = hh[i];
     const float Fx = fmav(-h, gpx, Rx[i]);
     bad |= !(h > 0.f) || !isfinite(Fx) || !isfinite(jx[i]);
-    collide<1, TAU1>(P, h, dd[i], jx[i], 0.f, Fx, 0.f, f_old[i], fs[i]);
+    collide<1, TAU1>(P, h, g0[i], sm[i], jx[i], 0.f, Fx, 0.f, f_old[i], fs[i]);
   }
   return bad;
 }
@@ -663,7 +786,7 @@ __global__ void __launch_bounds__(TX)
   const int x0 = blockIdx.x * TX, tx = threadIdx.x;
 
   const bool sub = P.sub_amp != 0.f;
-  float hh[N], dd[N], jx[N];
+  float hh[N], g0[N], sm[N], jx[N];
   {
     float z = sub ? substrate_at(P, x0 + tx, 0) : 0.f;
 #pragma unroll
@@ -672,7 +795,8 @@ __global__ void __launch_bounds__(TX)
       const float f1 = __ldg(fin + L.at(i * Q + 1, x0 + tx, 0));
       const float f2 = __ldg(fin + L.at(i * Q + 2, x0 + tx, 0));
       const float s = f0 + (f1 + f2);
-      dd[i] = s;
+      g0[i] = f0;
+      sm[i] = f1 + f2;
       hh[i] = P.H[i] + s;
       jx[i] = f1 - f2;
       z += s;
@@ -689,7 +813,7 @@ __global__ void __launch_bounds__(TX)
       const float f1 = __ldg(fin + L.at(i * Q + 1, x, 0));
       const float f2 = __ldg(fin + L.at(i * Q + 2, x, 0));
       z += f0 + (f1 + f2);
-      zs[i][rc] = z;
+      zs[i][chk_index(rc, RW)] = z;
     }
   }
   __syncthreads();
@@ -698,9 +822,9 @@ __global__ void __launch_bounds__(TX)
     float zw[N], zc[N], ze[N], p[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      zw[i] = zs[i][rc - 1];
-      zc[i] = zs[i][rc];
-      ze[i] = zs[i][rc + 1];
+      zw[i] = zs[i][chk_index(rc - 1, RW)];
+      zc[i] = zs[i][chk_index(rc, RW)];
+      ze[i] = zs[i][chk_index(rc + 1, RW)];
     }
     if (sub) {
       const int x = x0 - 1 + pc;
@@ -710,7 +834,7 @@ __global__ void __launch_bounds__(TX)
       d1q3_pressures<N, W32>(P, zw, zc, ze, p);
     }
 #pragma unroll
-    for (int i = 0; i < N; ++i) ps[i][pc] = p[i];
+    for (int i = 0; i < N; ++i) ps[i][chk_index(pc, PW)] = p[i];
   }
   __syncthreads();
   const int gx = x0 + tx;
@@ -724,7 +848,7 @@ __global__ void __launch_bounds__(TX)
 #pragma unroll
     for (int k = 0; k < Q; ++k) fo[i][k] = TAU1 ? 0.f : fin[L.at(i * Q + k, gx, 0)];
   }
-  const bool bad = d1q3_collide_cell<N, TAU1>(P, dd, hh, jx, pw, pc, pe, fo, fs);
+  const bool bad = d1q3_collide_cell<N, TAU1>(P, g0, sm, hh, jx, pw, pc, pe, fo, fs);
   int dxs[3], xis[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -769,7 +893,7 @@ __global__ void __launch_bounds__(kD1PT)
   float* psm = zsm + N * nx;          // [i][x]
   for (int t = tid; t < Q * N * nx; t += kD1PT) {
     const int pl = t / nx, x = t - pl * nx;
-    fa[t] = fin[L.at(pl, x, 0)];
+    *chk_smem(fa + t) = fin[L.at(pl, x, 0)];
   }
   __syncthreads();
   bool bad = false;
@@ -779,8 +903,9 @@ __global__ void __launch_bounds__(kD1PT)
       float z = P.sub_amp != 0.f ? substrate_at(P, x, 0) : 0.f;
 #pragma unroll
       for (int i = 0; i < N; ++i) {
-        z += fa[(i * Q + 0) * nx + x] + (fa[(i * Q + 1) * nx + x] + fa[(i * Q + 2) * nx + x]);
-        zsm[i * nx + x] = z;
+        z += *chk_smem(fa + (i * Q + 0) * nx + x) +
+             (*chk_smem(fa + (i * Q + 1) * nx + x) + *chk_smem(fa + (i * Q + 2) * nx + x));
+        *chk_smem(zsm + i * nx + x) = z;
       }
     }
     __syncthreads();
@@ -790,9 +915,9 @@ __global__ void __launch_bounds__(kD1PT)
       float zw[N], zc[N], ze[N], p[N];
 #pragma unroll
       for (int i = 0; i < N; ++i) {
-        zw[i] = zsm[i * nx + xw];
-        zc[i] = zsm[i * nx + x];
-        ze[i] = zsm[i * nx + xe];
+        zw[i] = *chk_smem(zsm + i * nx + xw);
+        zc[i] = *chk_smem(zsm + i * nx + x);
+        ze[i] = *chk_smem(zsm + i * nx + xe);
       }
       if (P.sub_amp != 0.f)
         d1q3_pressures<N, W32>(P, zw, zc, ze, p, substrate_at(P, x - 1, 0),
@@ -800,34 +925,36 @@ __global__ void __launch_bounds__(kD1PT)
       else
         d1q3_pressures<N, W32>(P, zw, zc, ze, p);
 #pragma unroll
-      for (int i = 0; i < N; ++i) psm[i * nx + x] = p[i];
+      for (int i = 0; i < N; ++i) *chk_smem(psm + i * nx + x) = p[i];
     }
     __syncthreads();
     // force, collision, streaming into fb
     for (int x = tid; x < nx; x += kD1PT) {
       const int xw = x == 0 ? nx - 1 : x - 1, xe = x == nx - 1 ? 0 : x + 1;
-      float dd[N], hh[N], jx[N], pw[N], pc[N], pe[N], fo[N][Q], fs[N][Q];
+      float g0[N], sm[N], hh[N], jx[N], pw[N], pc[N], pe[N], fo[N][Q], fs[N][Q];
 #pragma unroll
       for (int i = 0; i < N; ++i) {
-        const float f0 = fa[(i * Q + 0) * nx + x], f1 = fa[(i * Q + 1) * nx + x];
-        const float f2 = fa[(i * Q + 2) * nx + x];
+        const float f0 = *chk_smem(fa + (i * Q + 0) * nx + x);
+        const float f1 = *chk_smem(fa + (i * Q + 1) * nx + x);
+        const float f2 = *chk_smem(fa + (i * Q + 2) * nx + x);
         const float sum = f0 + (f1 + f2);
-        dd[i] = sum;
+        g0[i] = f0;
+        sm[i] = f1 + f2;
         hh[i] = P.H[i] + sum;
         jx[i] = f1 - f2;
         fo[i][0] = f0;
         fo[i][1] = f1;
         fo[i][2] = f2;
-        pw[i] = psm[i * nx + xw];
-        pc[i] = psm[i * nx + x];
-        pe[i] = psm[i * nx + xe];
+        pw[i] = *chk_smem(psm + i * nx + xw);
+        pc[i] = *chk_smem(psm + i * nx + x);
+        pe[i] = *chk_smem(psm + i * nx + xe);
       }
-      bad |= d1q3_collide_cell<N, TAU1>(P, dd, hh, jx, pw, pc, pe, fo, fs);
+      bad |= d1q3_collide_cell<N, TAU1>(P, g0, sm, hh, jx, pw, pc, pe, fo, fs);
       const int dst[3] = {x, xe, xw};  // c_k = 0, +1, -1
 #pragma unroll
       for (int i = 0; i < N; ++i)
 #pragma unroll
-        for (int k = 0; k < Q; ++k) fb[(i * Q + k) * nx + dst[k]] = fs[i][k];
+        for (int k = 0; k < Q; ++k) *chk_smem(fb + (i * Q + k) * nx + dst[k]) = fs[i][k];
     }
     __syncthreads();
     float* t = fa;
@@ -839,7 +966,7 @@ __global__ void __launch_bounds__(kD1PT)
     const int pl = t / (nx + 4), x = t - pl * (nx + 4) - 2;
     int sx = x % nx;
     sx += sx < 0 ? nx : 0;
-    fout[L.at(pl, x, 0)] = fa[pl * nx + sx];
+    fout[L.at(pl, x, 0)] = *chk_smem(fa + pl * nx + sx);
   }
   if (bad) atomicOr(status, kStatusNonfinite);
 }
@@ -873,8 +1000,19 @@ static cudaError_t launch_d2(const StepLaunch& a, cudaStream_t st) {
   const int ntiles = ((a.P.nx + T::TX - 1) / T::TX) * ((a.P.ny + T::TY - 1) / T::TY);
   const int slots = a.num_sms * per_sm[dev];
   const int grid = ntiles < slots ? ntiles : slots;
-  kern<<<grid, T::NT, T::kSmem, st>>>(*a.fin_map, a.fout, a.P, a.status, a.sched);
-  return cudaGetLastError();
+  // launched as a programmatic dependent of the previous kernel on the
+  // stream (see d2q9_tile_loop)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(T::NT);
+  cfg.dynamicSmemBytes = T::kSmem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, *a.fin_map, a.fout, a.P, a.status, a.sched, a.reverse);
 }
 
 int step_mode(const KParams& P) {
@@ -1022,5 +1160,7 @@ int step_tile_rows(int n, int lattice) {
     default: return D2Tile<5>::TY;
   }
 }
+
+MLSW_DEFINE_BOUNDS_READER(bounds_violations_step)
 
 }  // namespace mlsw

@@ -99,6 +99,7 @@ EXPORTS = {
     "mlswlbm_step_until": (ctypes.c_int, [_H, ctypes.c_long, ctypes.c_long, ctypes.c_double,
                                           ctypes.POINTER(ctypes.c_long), _D]),
     "mlswlbm_set_stream": (ctypes.c_int, [_H, ctypes.c_void_p]),
+    "mlswlbm_debug_bounds_violations": (ctypes.c_int, [ctypes.POINTER(ctypes.c_ulonglong)]),
     "mlswlbm_launch_count": (ctypes.c_long, [_H]),
     "mlswlbm_destroy": (None, [_H]),
     "mlswlbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -536,6 +537,17 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def mlswlbm_debug_bounds_violations():
+    """Accesses out of range counted by a bounds-checked build since the last
+    call (the counters are cleared), or None for a release build."""
+    n = ctypes.c_ulonglong(0)
+    rc = lib().mlswlbm_debug_bounds_violations(ctypes.byref(n))
+    if rc == MLSW_ERR_UNSUPPORTED:
+        return None
+    _check(rc, "mlswlbm_debug_bounds_violations")
+    return int(n.value)
 
 
 def selftest_bounded_wait(arrive, limit=256, stream=None):
