@@ -468,6 +468,74 @@ int mlswlbm_surrogate_debug(mlswlbm_surrogate* s, int what, void* out, long byte
 
 void mlswlbm_surrogate_destroy(mlswlbm_surrogate* s);
 
+/* ---------------------------------------------------------------------
+ * U-Net surrogate of 64 LBM steps on the 5th-generation tensor cores.
+ * Not a part of the paper's method: a learned stand-in for 64 steps of
+ * the LBM step above (same inputs and outputs as mlswlbm_surrogate_*),
+ * trained on trajectories the solver generates and judged by it.
+ *
+ * Network: four levels of 32, 64, 128 and 256 channels at full, 1/2, 1/4
+ * and 1/8 resolution; two 3 x 3 periodic convolutions with ReLU per level
+ * on the way down (2 x 2 average pooling between levels) and on the way up
+ * (nearest 2x upsampling, concatenated with the way down's features of the
+ * same level), then a 3 x 3 convolution to 16 channels whose first n are
+ * the layers' change times out_scale. Input planes (16): (h_i - mean h_i)
+ * in_scale, then the n_extra problem parameters as constant planes, then
+ * zeros. The change is made mean-free per layer, so every prediction keeps
+ * each layer's mass, as the LBM does.
+ * Arithmetic: BF16 activations and weights, FP32 accumulation in tensor
+ * memory (tcgen05.mma, operands staged by TMA), FP32 master weights and
+ * Adam moments. Arrays are device memory, [batch][n][ny][nx] FP32 unless
+ * stated; work is enqueued on the stream given at create.
+ * ------------------------------------------------------------------- */
+typedef struct mlswlbm_unet mlswlbm_unet;
+
+/* Number of FP32 parameters: for each of the 15 convolutions in order,
+ * its weights [out][tap][in] (tap = 3 (dy + 1) + (dx + 1)), then its bias. */
+long mlswlbm_unet_param_count(void);
+
+/* Creates a network for n_layers (1..MLSW_MAX_LAYERS) on nx x ny lattices
+ * (powers of two from 128 to 4096) and batches of up to max_batch samples;
+ * extra: n_extra values (host; n_layers + n_extra <= 16) for the parameter
+ * planes. He-normal weights from a generator seeded with `seed`, zero
+ * biases. Errors: MLSW_ERR_ARG, MLSW_ERR_UNSUPPORTED (lattice size),
+ * MLSW_ERR_NOMEM, MLSW_ERR_CUDA; *out is NULL on failure. */
+int mlswlbm_unet_create(int n_layers, int nx, int ny, int max_batch, int n_extra,
+                        const double* extra, unsigned long long seed, double in_scale,
+                        double out_scale, void* stream, mlswlbm_unet** out);
+
+/* out = h + the predicted, mass-projected change over 64 steps, for
+ * `batch` samples (device arrays; out may not alias h). Asynchronous. */
+int mlswlbm_unet_predict(mlswlbm_unet* u, const float* h, float* out, int batch);
+
+/* One Adam step (learning rate lr, betas 0.9 / 0.999, eps 1e-8) on the mean
+ * squared error between the first n output channels and (target - h)
+ * out_scale; *loss (optional, host) receives that error before the step,
+ * and the call then synchronises. */
+int mlswlbm_unet_train_step(mlswlbm_unet* u, const float* h, const float* target, int batch,
+                            double lr, double* loss);
+
+/* MLSW_ERR_TIMEOUT if a bounded wait of a tensor-core kernel ran out since
+ * create, else MLSW_OK. Synchronises. */
+int mlswlbm_unet_status(mlswlbm_unet* u);
+
+/* Parameters to / from host memory (count = mlswlbm_unet_param_count());
+ * setting them resets the Adam moments. Synchronise. */
+int mlswlbm_unet_set_params(mlswlbm_unet* u, const float* host, long count);
+int mlswlbm_unet_get_params(mlswlbm_unet* u, float* host, long count);
+
+/* Copies an internal array of the last pass to host memory, for tests:
+ * kind 0 the activation tensor `id`, kind 1 its gradient (BF16, NHWC with a
+ * one-pixel periodic halo, [max_batch][h + 2][w + 2][C]), kind 2 the
+ * parameter gradients (FP32), kind 3 the network output (FP32
+ * [max_batch][n][ny][nx]), kind 4 the gradient that reaches the way down's
+ * features of level `id` (0..2) through the skip connection. Tensor ids:
+ * X0 A0 S0 P1 A1 S1 P2 A2 S2 P3 A3 S3 U2 B2 D2 U1 B1 D1 U0 B0 D0 YG = 0..21
+ * (YG: the output gradient). Synchronises. */
+int mlswlbm_unet_debug(mlswlbm_unet* u, int kind, int id, void* out, long bytes);
+
+void mlswlbm_unet_destroy(mlswlbm_unet* u);
+
 #ifdef __cplusplus
 }
 #endif

@@ -583,6 +583,21 @@ EXPORTS_SURROGATE = {
     "mlswlbm_surrogate_debug": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                                ctypes.c_long]),
     "mlswlbm_surrogate_destroy": (None, [ctypes.c_void_p]),
+    "mlswlbm_unet_param_count": (ctypes.c_long, []),
+    "mlswlbm_unet_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_int, _D, ctypes.c_ulonglong, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_void_p,
+                                           ctypes.POINTER(ctypes.c_void_p)]),
+    "mlswlbm_unet_predict": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_int]),
+    "mlswlbm_unet_train_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_int, ctypes.c_double, _D]),
+    "mlswlbm_unet_status": (ctypes.c_int, [ctypes.c_void_p]),
+    "mlswlbm_unet_set_params": (ctypes.c_int, [ctypes.c_void_p, _F, ctypes.c_long]),
+    "mlswlbm_unet_get_params": (ctypes.c_int, [ctypes.c_void_p, _F, ctypes.c_long]),
+    "mlswlbm_unet_debug": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_void_p, ctypes.c_long]),
+    "mlswlbm_unet_destroy": (None, [ctypes.c_void_p]),
 }
 
 
@@ -674,4 +689,126 @@ class Surrogate:
         out = np.empty(shape, dtype=dtype)
         _check(_surr_lib().mlswlbm_surrogate_debug(self._s, int(what), out.ctypes.data, out.nbytes),
                "mlswlbm_surrogate_debug")
+        return out
+
+
+UNET_TENSORS = ("X0", "A0", "S0", "P1", "A1", "S1", "P2", "A2", "S2", "P3", "A3", "S3",
+                "U2", "B2", "D2", "U1", "B1", "D1", "U0", "B0", "D0", "YG")
+UNET_CHANNELS = (16, 32, 32, 32, 64, 64, 64, 128, 128, 128, 256, 256,
+                 256, 128, 128, 128, 64, 64, 64, 32, 32, 16)
+UNET_LEVELS = (0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3, 2, 2, 2, 1, 1, 1, 0, 0, 0, 0)
+
+
+class UNet:
+    """mlswlbm_unet_*: the U-Net surrogate of 64 LBM steps on tcgen05.
+    Device arrays are torch CUDA tensors of float32 [batch][n][ny][nx]."""
+
+    def __init__(self, n, nx, ny, max_batch, extra=(), seed=0, in_scale=20.0, out_scale=100.0,
+                 stream=None):
+        self.n, self.nx, self.ny, self.max_batch = int(n), int(nx), int(ny), int(max_batch)
+        self.in_scale, self.out_scale = float(in_scale), float(out_scale)
+        self.extra = [float(v) for v in extra]
+        ex = (ctypes.c_double * max(1, len(self.extra)))(*self.extra)
+        self._u = ctypes.c_void_p()
+        _check(lib().mlswlbm_unet_create(self.n, self.nx, self.ny, self.max_batch,
+                                         len(self.extra), ex, int(seed), self.in_scale,
+                                         self.out_scale, _stream_ptr(stream),
+                                         ctypes.byref(self._u)), "mlswlbm_unet_create")
+
+    def close(self):
+        if self._u:
+            lib().mlswlbm_unet_destroy(self._u)
+            self._u = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def param_count():
+        return int(lib().mlswlbm_unet_param_count())
+
+    def _batch(self, t):
+        import torch
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32
+                and t.is_contiguous()):
+            raise ValueError("float32 contiguous CUDA tensor expected")
+        if tuple(t.shape[1:]) != (self.n, self.ny, self.nx) or not 1 <= t.shape[0] <= self.max_batch:
+            raise ValueError("shape [batch][n][ny][nx] expected")
+        return int(t.shape[0])
+
+    def predict(self, h, out):
+        b = self._batch(h)
+        if tuple(out.shape) != tuple(h.shape):
+            raise ValueError("out must match h")
+        self._batch(out)
+        _check(lib().mlswlbm_unet_predict(self._u, ctypes.c_void_p(h.data_ptr()),
+                                          ctypes.c_void_p(out.data_ptr()), b),
+               "mlswlbm_unet_predict")
+        return out
+
+    def train_step(self, h, target, lr):
+        b = self._batch(h)
+        if tuple(target.shape) != tuple(h.shape):
+            raise ValueError("target must match h")
+        loss = ctypes.c_double()
+        _check(lib().mlswlbm_unet_train_step(self._u, ctypes.c_void_p(h.data_ptr()),
+                                             ctypes.c_void_p(target.data_ptr()), b, float(lr),
+                                             ctypes.byref(loss)), "mlswlbm_unet_train_step")
+        return loss.value
+
+    def status(self):
+        return int(lib().mlswlbm_unet_status(self._u))
+
+    def get_params(self):
+        out = np.empty(self.param_count(), dtype=np.float32)
+        _check(lib().mlswlbm_unet_get_params(self._u, _fptr(out), out.size),
+               "mlswlbm_unet_get_params")
+        return out
+
+    def set_params(self, w):
+        a = np.ascontiguousarray(w, dtype=np.float32)
+        _check(lib().mlswlbm_unet_set_params(self._u, _fptr(a), a.size),
+               "mlswlbm_unet_set_params")
+
+    def _tensor_shape(self, name):
+        i = UNET_TENSORS.index(name)
+        lev = UNET_LEVELS[i]
+        return i, (self.max_batch, (self.ny >> lev) + 2, (self.nx >> lev) + 2, UNET_CHANNELS[i])
+
+    def tensor(self, name, grad=False):
+        """An activation (or its gradient) of the last pass as float32
+        [max_batch][h + 2][w + 2][C], halo ring included."""
+        i, shape = self._tensor_shape(name)
+        out = np.empty(shape, dtype=np.uint16)
+        _check(lib().mlswlbm_unet_debug(self._u, 1 if grad else 0, i, out.ctypes.data, out.nbytes),
+               "mlswlbm_unet_debug")
+        return (out.astype(np.uint32) << 16).view(np.float32)
+
+    def skip_grad(self, level):
+        name = ("S0", "S1", "S2")[level]
+        _, shape = self._tensor_shape(name)
+        out = np.empty(shape, dtype=np.uint16)
+        _check(lib().mlswlbm_unet_debug(self._u, 4, int(level), out.ctypes.data, out.nbytes),
+               "mlswlbm_unet_debug")
+        return (out.astype(np.uint32) << 16).view(np.float32)
+
+    def param_grads(self):
+        out = np.empty(self.param_count(), dtype=np.float32)
+        _check(lib().mlswlbm_unet_debug(self._u, 2, 0, out.ctypes.data, out.nbytes),
+               "mlswlbm_unet_debug")
+        return out
+
+    def output(self):
+        out = np.empty((self.max_batch, self.n, self.ny, self.nx), dtype=np.float32)
+        _check(lib().mlswlbm_unet_debug(self._u, 3, 0, out.ctypes.data, out.nbytes),
+               "mlswlbm_unet_debug")
         return out
