@@ -107,7 +107,10 @@ def rollout(s, params, h0, windows, tau, hand_over=False):
     """Advances one instance by `windows` windows: the surrogate's window is
     taken when its predicted largest change is at most tau, otherwise the LBM
     runs the 64 steps, restarted from the current heights (all on the
-    device; one host read of the predicted change per window). With
+    device; one host read of the predicted change per window). A restart
+    sets the populations to f_eq(h, U = 0): the layer fluxes of the previous
+    LBM window are not carried over, so the LBM windows of a rollout are
+    not the uninterrupted LBM trajectory from the same heights. With
     hand_over, the first window the surrogate does not take hands all the
     remaining windows to the LBM in one call (a film whose change has grown
     past tau keeps changing faster until it has dewetted). Returns (heights,
@@ -140,9 +143,13 @@ def rollout(s, params, h0, windows, tau, hand_over=False):
 
 
 def lbm_rollout(params, h0, windows):
-    """The same windows by the LBM alone (one solver, no restarts)."""
+    """The same windows by the LBM alone (one solver, no restarts), timed
+    like rollout(): on torch's current stream, from a synchronised start."""
+    torch = _torch()
     host = np.empty((int(params["n"]), int(params["ny"]), int(params["nx"])), dtype=np.float32)
-    with B.Solver(params, np.asarray(h0, dtype=np.float32)) as lbm:
+    with B.Solver(params, np.asarray(h0, dtype=np.float32),
+                  stream=torch.cuda.current_stream()) as lbm:
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
         lbm.step(WINDOW * windows)
         lbm.get_heights(host)
