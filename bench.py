@@ -30,7 +30,9 @@ Two more workloads are reported beside the main line, under "workloads"
     chip) and heights read back, wall clock;
   * three-layer lens field, D2Q9, 2048 x 2048, lenses of radius 200 (the
     droplet/lens equilibrium workload): LSU/s over event-timed
-    back-to-back steps; its 2 x 906 MB working set exceeds the L2;
+    back-to-back steps (its 2 x 906 MB working set exceeds the L2), then
+    the run until the kinetic energy falls below 1e-12 (at most 500 000
+    steps) with the lenses' Neumann angles;
   * batched stability sweep: 512 instances (2..5 layers, sides 64..512,
     ~142 M layer-sites per step) in one batch with the tile-height
     autotuner: LSU/s of the batched step, the time to solution of 2000
@@ -39,10 +41,10 @@ Two more workloads are reported beside the main line, under "workloads"
     with one solver each (20 steps per instance, scaled to 2000);
   * analysis on the device, 1024^2 film: radial power spectra of the layers
     and ring means of the interfaces, wall time per call;
-  * the convolutional surrogate of 64 LBM steps on the 64^2 two-layer
-    dewetting film: training on solver trajectories, held-out errors against
-    the LBM and the identity map, time per window, a rollout with LBM
-    fallback.
+  * the U-Net surrogate of 64 LBM steps on the 256^2 three-layer film:
+    training on 20 000 solver trajectories, held-out errors against the LBM
+    and the identity map, tensor-core throughput, and the time to solution
+    of 64 instances judged by the LBM against batched and per-instance LBM.
 
 Reference arm (--impl reference): the FP64 CPU oracle on the host cores, one
 oracle step per benchmark step on a 128 x 128 patch with the same recipe.
@@ -436,10 +438,28 @@ def extra_workloads(B, torch):
             "steps_per_s": 10000 / (t1 - t0), "gpu_launches": int(s.launch_count() - l0),
             "note": "mlswlbm_step(10000) + mlswlbm_get_heights, wall clock",
             "finite": bool(np.isfinite(h).all())}
+    out["lens3_d2q9_2048"] = lens_workload(B, torch)
+    out["stability_sweep_512"] = sweep_workload(B, torch)
+    out["analysis_film3_1024"] = analysis_workload(B)
+    out["unet_surrogate_film3_256"] = unet_workload(B, torch)
+    return out
+
+
+def lens_workload(B, torch, max_steps=500000, check_every=5000, ke_stop=1e-12):
+    """The droplet/lens equilibrium workload: four three-layer lenses of
+    base radius 200 on the 2048^2 D2Q9 lattice. LBM throughput over 100
+    back-to-back steps, then the run to equilibrium: mlswlbm_step_until
+    until the kinetic energy falls below 1e-12 or 500 000 steps, wall clock,
+    and the upper and lower Neumann angles of every lens from the device's
+    ring means and the library's arc fit (target 20 degrees; the FP64
+    oracle's 128^2 version of the workload gives 18.7-19.3)."""
     side, radius, steps = 2048, 200.0, 100
     p = workloads.lens3_params(side, side, radius)
     h0 = workloads.lens3_heights(side, side, radius)
     st = torch.cuda.current_stream()
+    lsu = 3 * side * side
+    peak, _ = hbm_peak()
+    res = {}
     with B.Solver(p, h0, stream=st) as s:
         s.step(5)
         torch.cuda.synchronize()
@@ -449,90 +469,131 @@ def extra_workloads(B, torch):
         e1.record(st)
         torch.cuda.synchronize()
         dt = e0.elapsed_time(e1) * 1e-3 / steps
-        lsu = 3 * side * side
-        peak, _ = hbm_peak()
-        out["lens3_d2q9_2048"] = {
-            "value": lsu / dt, "unit": UNIT, "ms_per_step": 1e3 * dt, "steps": steps,
-            "roofline_frac": BYTES_PER_LSU * lsu / dt / 1e9 / peak,
-            "l2": "back-to-back steps; 2 x 906 MB working set > 129 MB L2",
-            "status": B.mlswlbm_strerror(s.status())}
-    out["stability_sweep_512"] = sweep_workload(B, torch)
-    out["analysis_film3_1024"] = analysis_workload(B)
-    out["surrogate_dewet2_64"] = surrogate_workload(B, torch)
-    return out
-
-
-def surrogate_workload(B, torch):
-    """The convolutional surrogate of 64 LBM steps on the two-layer 64^2
-    dewetting film: trajectories of 64 seeded instances (150 windows of 64
-    steps, through rupture), 6000 training steps on 56 of them, errors on the
-    other 8 against the LBM and against the identity map, time per window,
-    and a rollout that falls back to the LBM when the predicted change
-    exceeds the threshold calibrated on the training windows."""
-    from paper_2409_16659_gb300 import surrogate as S
-    side, ninst, nwin = 64, 64, 150
-    params = [workloads.dewet2_params(side) for _ in range(ninst)]
-    heights = [workloads.dewet2_heights(side, seed=100 + j).astype(np.float32) for j in range(ninst)]
-    res = {}
-    t0 = time.perf_counter()
-    traj = S.trajectories(params, heights, nwin)
-    torch.cuda.synchronize()
-    res["trajectories_s"] = time.perf_counter() - t0
-    train_idx, test_idx = list(range(56)), list(range(56, 64))
-    late = slice(90, None)  # windows from step 5760 on: rupture and coarsening
-    with B.Surrogate(2, side, side, 32, seed=1, in_scale=10.0, out_scale=40.0) as s:
+        res.update({"value": lsu / dt, "unit": UNIT, "ms_per_step": 1e3 * dt, "steps": steps,
+                    "roofline_frac": BYTES_PER_LSU * lsu / dt / 1e9 / peak,
+                    "l2": "back-to-back steps; 2 x 906 MB working set > 129 MB L2"})
         t0 = time.perf_counter()
-        losses = S.train(s, traj, train_idx, 6000, 32, 2e-3, 1e-4, seed=2)
-        res["train_s"] = time.perf_counter() - t0
-        res["loss_start_end"] = [float(losses[:20].mean()), float(losses[-50:].mean())]
-        err, ident, _ = S.window_errors(s, traj, test_idx)
-        etr, _, ctr = S.window_errors(s, traj, train_idx[:16])
-        res["held_out"] = {
-            "frac_windows_err_le_1e-3": float((err <= 1e-3).mean()),
-            "identity_frac_le_1e-3": float((ident <= 1e-3).mean()),
-            "nonlinear_median_err": float(np.median(err[:, late])),
-            "identity_nonlinear_median": float(np.median(ident[:, late])),
-            "nonlinear_frac_le_1e-3": float((err[:, late] <= 1e-3).mean())}
-        h1 = traj[56:57, 100].contiguous()
-        o1 = torch.empty_like(h1)
-        h32 = traj[24:56, 100].contiguous()
-        o32 = torch.empty_like(h32)
-        for _ in range(5):
-            s.predict(h1, o1)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(50):
-            s.predict(h1, o1)
-        torch.cuda.synchronize()
+        done, ke = s.step_until(max_steps, check_every, ke_stop)
         t1 = time.perf_counter()
-        for _ in range(20):
-            s.predict(h32, o32)
+        nb = int(1.6 * radius)
+        upper, lower = [], []
+        for c in workloads.lens3_centres(side, side, radius):
+            prof, cnt = s.radial_profile(c, nb)
+            up = prof[3] - prof[3][-3:].mean()
+            lo = prof[2][-3:].mean() - prof[2]
+            upper.append(B.fit_cap_angle(up, cnt, 0.0))
+            lower.append(B.fit_cap_angle(lo, cnt, 0.0))
+        res["to_equilibrium"] = {
+            "steps": int(done + steps + 5), "seconds": t1 - t0, "kinetic_energy": ke,
+            "stopped_by": "kinetic energy" if ke < ke_stop else "step cap",
+            "ke_threshold": ke_stop, "step_cap": max_steps,
+            "upper_angles_deg": [a for a, _ in upper], "lower_angles_deg": [a for a, _ in lower],
+            "arc_fit_errors": [e for _, e in upper + lower],
+            "neumann_angle_deg": 20.0}
+        res["status"] = B.mlswlbm_strerror(s.status())
+    return res
+
+
+def unet_workload(B, torch):
+    """The U-Net surrogate of 64 LBM steps on the three-layer spinodal film
+    (the 1024^2 benchmark recipe at 256^2; 3 height planes and 5 parameter
+    planes):
+      * training on 20 000 seeded trajectories of 4 windows each, made by the
+        batched solver 256 at a time and dropped after their Adam steps;
+      * errors of 64 held-out trajectories over 16 windows against the LBM,
+        next to the identity map's (the window's own change);
+      * tensor-core throughput of prediction and training;
+      * time to solution of 64 instances over 16 windows (1024 steps): the
+        U-Net judged by the LBM every 4th window (bound 1e-3), the batched
+        solver, and one solver per instance, with the largest height
+        difference from the batched solver's result."""
+    from paper_2409_16659_gb300 import surrogate as S
+    side, n = 256, 3
+    p = workloads.film3_d2q9_params(side, side)
+    extra = workloads.film3_unet_planes(p)
+    ntraj, chunk, windows, batch = 20000, 250, 4, 32
+    nchunks = ntraj // chunk
+    steps_per_chunk = chunk * windows // batch
+    st = torch.cuda.current_stream()
+    res = {"trajectories": nchunks * chunk, "windows_per_trajectory": windows,
+           "train_batch": batch}
+    with B.UNet(n, side, side, batch, extra=extra, seed=1, in_scale=1.0, out_scale=4.0,
+                stream=st) as u:
+        stream_t = S.TrajectoryStream([p] * chunk,
+                                      workloads.film3_d2q9_heights_device(side, side, chunk, 1),
+                                      windows, stream=st)
+        gen_s = [0.0]
+
+        def make_chunk(k):
+            t0 = time.perf_counter()
+            tr = stream_t(workloads.film3_d2q9_heights_device(side, side, chunk, 1000 + k))
+            torch.cuda.synchronize()
+            gen_s[0] += time.perf_counter() - t0
+            return tr
+
+        t0 = time.perf_counter()
+        losses = S.train_streaming(u, make_chunk, nchunks, steps_per_chunk, batch, 2e-3, 2e-4,
+                                   seed=5)
         torch.cuda.synchronize()
-        t2 = time.perf_counter()
-        with B.Solver(params[0], heights[0]) as lbm:
-            lbm.step(S.WINDOW)
-            torch.cuda.synchronize()
-            t3 = time.perf_counter()
-            for _ in range(20):
-                lbm.step(S.WINDOW)
-            torch.cuda.synchronize()
-            t4 = time.perf_counter()
-        res["window_us"] = {"surrogate_1": 1e6 * (t1 - t0) / 50,
-                            "surrogate_per_sample_in_32": 1e6 * (t2 - t1) / 20 / 32,
-                            "lbm_64_steps": 1e6 * (t4 - t3) / 20}
-        tau = S.calibrate(etr, ctr)
-        hr, taken, secs = S.rollout(s, params[60], heights[60], nwin, tau)
-        hh, taken_h, secs_h = S.rollout(s, params[60], heights[60], nwin, tau, hand_over=True)
-        hl, secs_l = S.lbm_rollout(params[60], heights[60], nwin)
-        hs = params[60]["hstar"]
-        res["rollout"] = {"windows": nwin, "tau": tau, "surrogate_windows": taken,
-                          "s": secs, "lbm_only_s": secs_l,
-                          "surrogate_stats": S.film_statistics(hr, hs),
-                          "lbm_stats": S.film_statistics(hl, hs),
-                          "hand_over": {"surrogate_windows": taken_h, "s": secs_h,
-                                        "stats": S.film_statistics(hh, hs)}}
-    res["note"] = ("errors are the largest height difference per window of 64 steps; the "
-                   "nonlinear windows start at step 5760, before rupture (~7200)")
+        res["train_s"] = time.perf_counter() - t0 - gen_s[0]
+        res["trajectories_s"] = gen_s[0]
+        stream_t.close()
+        res["loss_start_end"] = [float(losses[:20].mean()), float(losses[-50:].mean())]
+        # held-out trajectories: other seeds, 16 windows
+        hold = S.TrajectoryStream([p] * 64, workloads.film3_d2q9_heights_device(side, side, 64, 7),
+                                  16, stream=st)
+        traj = hold(workloads.film3_d2q9_heights_device(side, side, 64, 99991))
+        hold.close()
+        err, ident = S.unet_window_errors(u, traj)
+        res["held_out"] = {
+            "max_err_per_window": [float(v) for v in err.max(axis=0)],
+            "identity_max_err_per_window": [float(v) for v in ident.max(axis=0)],
+            "median_err_over_identity": float(np.median(err / ident)),
+            "frac_windows_err_le_1e-3": float((err <= 1e-3).mean()),
+            "identity_frac_le_1e-3": float((ident <= 1e-3).mean())}
+        # throughput of the tensor-core kernels
+        h = traj[:batch, 0].contiguous()
+        t = traj[:batch, 1].contiguous()
+        o = torch.empty_like(h)
+        for _ in range(3):
+            u.predict(h, o)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(st)
+        for _ in range(10):
+            u.predict(h, o)
+        e[1].record(st)
+        for _ in range(10):
+            u.train_step(h, t, 0.0)
+        e[2].record(st)
+        torch.cuda.synchronize()
+        fwd_flop = 22.347e9 * batch   # the 15 convolutions of one 256^2 sample, x batch
+        pm, tm = e[0].elapsed_time(e[1]) / 10, e[1].elapsed_time(e[2]) / 10
+        res["tensor_cores"] = {"predict_ms_batch32": pm, "train_step_ms_batch32": tm,
+                               "predict_tflops": fwd_flop / pm / 1e9,
+                               "train_tflops": 3 * fwd_flop / tm / 1e9,
+                               "note": "22.35 GFLOP per sample forward; training counted as 3x"}
+        # time to solution, 64 instances x 16 windows
+        params = [p] * 64
+        h0s = [np.asarray(workloads.film3_d2q9_heights(side, side, seed=50000 + j), np.float32)
+               for j in range(64)]
+        ref, t_batch = S.lbm_batched(params, h0s, 16, stream=st)
+        _, t_per = S.lbm_per_instance(params, h0s, 16, stream=st)
+        hr, info = S.judged_rollout(u, params, h0s, 16, audit_every=4, bound=1e-3, stream=st)
+        res["time_to_solution"] = {
+            "instances": 64, "windows": 16, "steps": 1024,
+            "surrogate_judged_s": info["seconds"], "lbm_batched_s": t_batch,
+            "lbm_per_instance_s": t_per,
+            "speedup_vs_per_instance": t_per / info["seconds"],
+            "speedup_vs_batched": t_batch / info["seconds"],
+            "surrogate_windows": info["surrogate_windows"],
+            "audited_windows": info["audited_windows"],
+            "fallback_instances": info["fallback_instances"],
+            "max_audit_err": float(max(info["audit_errors"])) if info["audit_errors"] else None,
+            "final_max_height_diff_vs_lbm": float((hr - ref).abs().max()),
+            "note": "every 4th window and the last judged by the batched LBM from the same "
+                    "heights; an instance beyond 1e-3 returns to its last passed audit and "
+                    "finishes on the LBM"}
+        res["status"] = u.status()
     return res
 
 
@@ -658,6 +719,29 @@ def run_profile(args):
     return 0
 
 
+def run_profile_unet(args):
+    """The U-Net surrogate at 256^2, batch 8: --warmup predictions, then
+    --steps predictions and one training step (for ncu captures of the
+    convolution kernels: 15 launches of conv_tc per prediction, the
+    13th being the largest level-0 one, 96 -> 32 channels)."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2409_16659_gb300 import mlswlbm as B
+    side, batch = 256, 8
+    p = workloads.film3_d2q9_params(side, side)
+    st = torch.cuda.current_stream()
+    with B.UNet(3, side, side, batch, extra=workloads.film3_unet_planes(p), seed=1,
+                in_scale=1.0, out_scale=4.0, stream=st) as u:
+        h = workloads.film3_d2q9_heights_device(side, side, batch, 5)
+        out = torch.empty_like(h)
+        for _ in range(args.warmup + args.steps):
+            u.predict(h, out)
+        u.train_step(h, out, 0.0)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_unet_run": True, "status": u.status()}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -671,6 +755,8 @@ def main():
                     help="only warm-up + --steps back-to-back steps (for ncu captures)")
     ap.add_argument("--profile-batch", action="store_true",
                     help="the same for a 64-instance batch of the stability sweep")
+    ap.add_argument("--profile-unet", action="store_true",
+                    help="U-Net predictions at 256^2 (for ncu captures of its convolutions)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -680,6 +766,8 @@ def main():
         return run_profile(args)
     if args.profile_batch:
         return run_profile_batch(args)
+    if args.profile_unet:
+        return run_profile_unet(args)
     return run_own(args)
 
 

@@ -394,6 +394,15 @@ int mlswlbm_batch_step(mlsw_batch* b, long nsteps);
  * mlswlbm_get_heights (for the whole batch). MLSW_ERR_ARG for a bad index. */
 int mlswlbm_batch_get_heights(mlsw_batch* b, int index, float* out);
 
+/* Device variants for one instance (dev: device, [n][ny][nx] FP32),
+ * asynchronous on the batch's stream. get writes the instance's heights;
+ * set restarts the instance from the given heights at rest, f = f_eq(h,
+ * U = 0) as at create (the rest-population shift of create is kept), and
+ * ORs MLSW_ERR_NONFINITE into the batch status where h <= 0 or h is not
+ * finite. MLSW_ERR_ARG for a bad index or NULL pointer. */
+int mlswlbm_batch_get_heights_device(mlsw_batch* b, int index, float* dev);
+int mlswlbm_batch_set_heights_device(mlsw_batch* b, int index, const float* dev);
+
 /* One Fourier mode of every layer of every instance:
  * out[2 (j MLSW_MAX_LAYERS + i) + 0 / 1] = Re / Im of
  * sum_{x,y} h_i(x, y) exp(-2 pi i (kx[j] x / nx_j + ky[j] y / ny_j)),
@@ -408,6 +417,18 @@ int mlswlbm_batch_status(mlsw_batch* b);
 /* Tile rows (8 or 16) that instance index runs with, or MLSW_ERR_ARG. */
 int mlswlbm_batch_tile_rows(const mlsw_batch* b, int index);
 
+/* Chooses the instances that mlswlbm_batch_step advances: the nsel distinct
+ * indices (host ints, 0 <= index < count; nsel = 0 leaves none, and the
+ * step then does nothing). Every instance starts selected. An instance left
+ * out keeps its state unchanged through later steps, and its heights can be
+ * read and set as before; selected again, it continues from that state.
+ * A selected instance steps with exactly the arithmetic it has in the full
+ * batch. Synchronises the batch's stream and rebuilds the step's launch
+ * plan (milliseconds): meant for occasional changes, such as dropping the
+ * instances that a caller finishes another way. MLSW_ERR_ARG for an index
+ * out of range, a repeated index, or nsel outside [0, count]. */
+int mlswlbm_batch_select(mlsw_batch* b, int nsel, const int* indices);
+
 /* Kernel launches issued since create (graph replays counted by the
  * kernels they contain), and groups (launches per step). */
 long mlswlbm_batch_launch_count(const mlsw_batch* b);
@@ -416,62 +437,9 @@ int mlswlbm_batch_groups(const mlsw_batch* b);
 void mlswlbm_batch_destroy(mlsw_batch* b);
 
 /* ---------------------------------------------------------------------
- * Surrogate of 64 LBM steps: a small convolutional network that maps the
- * layer heights h(t) of a periodic lattice to h(t + 64 steps), trained on
- * trajectories of the solver. Three 5 x 5 convolutions with periodic
- * padding, 16 -> 32 -> 32 -> 16 channels, ReLU between them; the input
- * channels are h_i - mean(h_i) times in_scale (zero channels up to 16), the
- * first n outputs the change over 64 steps times out_scale. The predicted
- * change is made mean-free per layer, so the prediction conserves every
- * layer's mass like the LBM does. BF16 weights and activations, FP32
- * accumulation on the tensor cores (warp-level mma.sync); FP32 master
- * parameters and Adam moments. All arrays are device memory in the layout
- * of mlswlbm_get_heights_device ([batch][n][ny][nx] FP32) unless stated;
- * work is enqueued on the stream given at create.
- * ------------------------------------------------------------------- */
-typedef struct mlswlbm_surrogate mlswlbm_surrogate;
-
-/* Number of FP32 parameters (weights [d][in][out] of the three layers, then
- * their biases). */
-long mlswlbm_surrogate_param_count(void);
-
-/* Creates a network for n_layers (1..MLSW_MAX_LAYERS) on nx x ny lattices
- * (nx a multiple of 16) and batches of up to max_batch samples; He-normal
- * weights from a generator seeded with `seed`, zero biases. MLSW_ERR_ARG,
- * MLSW_ERR_NOMEM; *out is NULL on failure. */
-int mlswlbm_surrogate_create(int n_layers, int nx, int ny, int max_batch, unsigned long long seed,
-                             double in_scale, double out_scale, void* stream,
-                             mlswlbm_surrogate** out);
-
-/* out = h + the predicted, mass-projected change over 64 steps, for `batch`
- * samples (device arrays; out may not alias h). Asynchronous. */
-int mlswlbm_surrogate_predict(mlswlbm_surrogate* s, const float* h, float* out, int batch);
-
-/* One Adam step (learning rate lr, betas 0.9 / 0.999) on the mean squared
- * error between the network's change and (target - h) out_scale over the n
- * layers; *loss (optional, host) receives that error before the step and
- * then the call synchronises. */
-int mlswlbm_surrogate_train_step(mlswlbm_surrogate* s, const float* h, const float* target,
-                                 int batch, double lr, double* loss);
-
-/* Parameters to / from host memory (count = mlswlbm_surrogate_param_count());
- * setting them also resets the Adam moments. Synchronise. */
-int mlswlbm_surrogate_set_params(mlswlbm_surrogate* s, const float* host, long count);
-int mlswlbm_surrogate_get_params(mlswlbm_surrogate* s, float* host, long count);
-
-/* Copies an internal buffer of the last forward / training pass to host
- * memory, for tests: 0 network output (FP32 [pixel][16]), 1 parameter
- * gradient (FP32), 2 input (BF16 [pixel][16]), 3 and 4 hidden activations
- * (BF16 [pixel][32]), 5 output gradient (BF16 [pixel][16]), 6 and 7 the
- * gradients of the hidden activations (second, then first). Synchronises. */
-int mlswlbm_surrogate_debug(mlswlbm_surrogate* s, int what, void* out, long bytes);
-
-void mlswlbm_surrogate_destroy(mlswlbm_surrogate* s);
-
-/* ---------------------------------------------------------------------
  * U-Net surrogate of 64 LBM steps on the 5th-generation tensor cores.
  * Not a part of the paper's method: a learned stand-in for 64 steps of
- * the LBM step above (same inputs and outputs as mlswlbm_surrogate_*),
+ * the LBM step above (heights in, heights 64 steps later out),
  * trained on trajectories the solver generates and judged by it.
  *
  * Network: four levels of 32, 64, 128 and 256 channels at full, 1/2, 1/4
@@ -479,10 +447,12 @@ void mlswlbm_surrogate_destroy(mlswlbm_surrogate* s);
  * on the way down (2 x 2 average pooling between levels) and on the way up
  * (nearest 2x upsampling, concatenated with the way down's features of the
  * same level), then a 3 x 3 convolution to 16 channels whose first n are
- * the layers' change times out_scale. Input planes (16): (h_i - mean h_i)
- * in_scale, then the n_extra problem parameters as constant planes, then
- * zeros. The change is made mean-free per layer, so every prediction keeps
- * each layer's mass, as the LBM does.
+ * the layers' change times out_scale / s. Every sample is normalised by the
+ * RMS s of its deviations h_i - mean h_i over all its layers (a flat
+ * sample, s = 0, does not change). Input planes (16): (h_i - mean h_i)
+ * in_scale / s, then the n_extra problem parameters as constant planes,
+ * then zeros. The change is made mean-free per layer, so every prediction
+ * keeps each layer's mass, as the LBM does.
  * Arithmetic: BF16 activations and weights, FP32 accumulation in tensor
  * memory (tcgen05.mma, operands staged by TMA), FP32 master weights and
  * Adam moments. Arrays are device memory, [batch][n][ny][nx] FP32 unless
@@ -509,9 +479,9 @@ int mlswlbm_unet_create(int n_layers, int nx, int ny, int max_batch, int n_extra
 int mlswlbm_unet_predict(mlswlbm_unet* u, const float* h, float* out, int batch);
 
 /* One Adam step (learning rate lr, betas 0.9 / 0.999, eps 1e-8) on the mean
- * squared error between the first n output channels and (target - h)
- * out_scale; *loss (optional, host) receives that error before the step,
- * and the call then synchronises. */
+ * squared error between the first n output channels and
+ * (target - h) out_scale / s; *loss (optional, host) receives that error
+ * before the step, and the call then synchronises. */
 int mlswlbm_unet_train_step(mlswlbm_unet* u, const float* h, const float* target, int batch,
                             double lr, double* loss);
 

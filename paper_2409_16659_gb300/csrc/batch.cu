@@ -35,6 +35,10 @@ struct mlsw_batch {
   int count;
   std::vector<BatchInst> hinst;  // host copies of the descriptors
   std::vector<int> variant;      // tile-height variant of every instance
+  // instances the step advances (mlswlbm_batch_select; all at create) and,
+  // for one left out, the buffer index that holds its state
+  std::vector<char> selected;
+  std::vector<int> home;
   std::vector<Group> groups;
   BatchInst* dinst;
   int2* dtable;
@@ -65,6 +69,29 @@ int tiles_of(const BatchInst& b, int variant) {
   return b.ntx * ((b.P.ny + ty - 1) / ty);
 }
 
+// the buffer that holds instance j's state now
+int state_buffer(const mlsw_batch* b, int j) { return b->selected[j] ? b->cur : b->home[j]; }
+
+// Moves every left-out instance whose state sits in the other buffer to the
+// current one by swapping its two buffers (and their tensor maps) in its
+// descriptor, so that every instance's state is in buffer cur.
+int align_buffers(mlsw_batch* b) {
+  bool changed = false;
+  for (int j = 0; j < b->count; ++j) {
+    if (b->selected[j] || b->home[j] == b->cur) continue;
+    BatchInst& bi = b->hinst[j];
+    std::swap(bi.f[0], bi.f[1]);
+    for (int v = 0; v < mlsw::kBatchVariants; ++v) std::swap(bi.map[v][0], bi.map[v][1]);
+    b->home[j] = b->cur;
+    changed = true;
+  }
+  // pageable source: the copy is staged before the call returns
+  if (changed)
+    CUB(cudaMemcpyAsync(b->dinst, b->hinst.data(), (size_t)b->count * sizeof(BatchInst),
+                        cudaMemcpyHostToDevice, b->stream));
+  return MLSW_OK;
+}
+
 // (re)initialise every instance from its heights: f = f_eq(h, U = 0)
 int init_all(mlsw_batch* b, const float* const* h_init) {
   for (int j = 0; j < b->count; ++j) {
@@ -76,6 +103,7 @@ int init_all(mlsw_batch* b, const float* const* h_init) {
     CUB(mlsw::launch_init(kQ, P.n, P.L, true, b->hbuf, b->hinst[j].f[0], sh, b->dstatus,
                           b->stream));
     b->launches += 1;
+    b->home[j] = 0;
   }
   b->cur = 0;
   return MLSW_OK;
@@ -85,6 +113,7 @@ int init_all(mlsw_batch* b, const float* const* h_init) {
 int build_groups(mlsw_batch* b) {
   std::map<std::tuple<int, int, int>, std::vector<int>> members;
   for (int j = 0; j < b->count; ++j) {
+    if (!b->selected[j]) continue;
     const KParams& P = b->hinst[j].P;
     members[std::make_tuple(P.n, mlsw::step_mode(P), b->variant[j])].push_back(j);
   }
@@ -269,6 +298,8 @@ int mlswlbm_batch_create(int count, const mlsw_params* params, const float* cons
   try {
     b->hinst.resize(count);
     b->variant.resize(count);
+    b->selected.assign(count, 1);
+    b->home.assign(count, 0);
   } catch (...) {
     delete b;
     return MLSW_ERR_NOMEM;
@@ -369,6 +400,7 @@ int mlswlbm_batch_create(int count, const mlsw_params* params, const float* cons
 
 int mlswlbm_batch_step(mlsw_batch* b, long nsteps) {
   if (!b || nsteps < 0) return MLSW_ERR_ARG;
+  if (b->groups.empty()) return MLSW_OK;  // no instance selected
   for (long s = 0; s < nsteps; ++s) {
     CUB(cudaGraphLaunch(b->gexec[b->cur], b->stream));
     b->launches += (long)b->groups.size();
@@ -392,15 +424,35 @@ int mlswlbm_batch_status(mlsw_batch* b) {
 int mlswlbm_batch_get_heights(mlsw_batch* b, int index, float* out) {
   if (!b || !out || index < 0 || index >= b->count) return MLSW_ERR_ARG;
   const KParams& P = b->hinst[index].P;
-  CUB(mlsw::launch_batch_heights(&b->hinst[index], b->cur, b->hbuf, b->stream));
+  CUB(mlsw::launch_batch_heights(&b->hinst[index], state_buffer(b, index), b->hbuf, b->stream));
   b->launches += 1;
   CUB(cudaMemcpyAsync(out, b->hbuf, (size_t)P.n * P.nx * P.ny * sizeof(float),
                       cudaMemcpyDeviceToHost, b->stream));
   return mlswlbm_batch_status(b);
 }
 
+int mlswlbm_batch_get_heights_device(mlsw_batch* b, int index, float* dev_out) {
+  if (!b || !dev_out || index < 0 || index >= b->count) return MLSW_ERR_ARG;
+  CUB(mlsw::launch_batch_heights(&b->hinst[index], state_buffer(b, index), dev_out, b->stream));
+  b->launches += 1;
+  return MLSW_OK;
+}
+
+int mlswlbm_batch_set_heights_device(mlsw_batch* b, int index, const float* dev_in) {
+  if (!b || !dev_in || index < 0 || index >= b->count) return MLSW_ERR_ARG;
+  const KParams& P = b->hinst[index].P;
+  mlsw::KShift sh;
+  for (int i = 0; i < mlsw::kMaxLayers; ++i) sh.H[i] = P.H[i];
+  CUB(mlsw::launch_init(kQ, P.n, P.L, true, dev_in, b->hinst[index].f[state_buffer(b, index)],
+                        sh, b->dstatus, b->stream));
+  b->launches += 1;
+  return MLSW_OK;
+}
+
 int mlswlbm_batch_modes(mlsw_batch* b, const int* kx, const int* ky, double* out) {
   if (!b || !kx || !ky || !out) return MLSW_ERR_ARG;
+  const int rc = align_buffers(b);
+  if (rc != MLSW_OK) return rc;
   const size_t nk = (size_t)b->count * sizeof(int);
   CUB(cudaMemcpyAsync(b->dk, kx, nk, cudaMemcpyHostToDevice, b->stream));
   CUB(cudaMemcpyAsync(b->dk + b->count, ky, nk, cudaMemcpyHostToDevice, b->stream));
@@ -410,6 +462,35 @@ int mlswlbm_batch_modes(mlsw_batch* b, const int* kx, const int* ky, double* out
   CUB(cudaMemcpyAsync(out, b->dmode, 2 * (size_t)mlsw::kMaxLayers * b->count * sizeof(double),
                       cudaMemcpyDeviceToHost, b->stream));
   return mlswlbm_batch_status(b);
+}
+
+int mlswlbm_batch_select(mlsw_batch* b, int nsel, const int* indices) {
+  if (!b || nsel < 0 || nsel > b->count || (nsel > 0 && !indices)) return MLSW_ERR_ARG;
+  std::vector<char> want(b->count, 0);
+  for (int k = 0; k < nsel; ++k) {
+    const int j = indices[k];
+    if (j < 0 || j >= b->count || want[j]) return MLSW_ERR_ARG;
+    want[j] = 1;
+  }
+  // every state into buffer cur first: then leaving out or taking back an
+  // instance moves no data
+  int rc = align_buffers(b);
+  if (rc != MLSW_OK) return rc;
+  for (int j = 0; j < b->count; ++j) {
+    b->selected[j] = want[j];
+    b->home[j] = b->cur;
+  }
+  // the step graphs read the tile table being replaced
+  CUB(cudaStreamSynchronize(b->stream));
+  for (int k = 0; k < 2; ++k)
+    if (b->gexec[k]) {
+      cudaGraphExecDestroy(b->gexec[k]);
+      b->gexec[k] = nullptr;
+    }
+  rc = build_groups(b);
+  if (rc == MLSW_OK && !b->groups.empty()) rc = capture_step(b, 0, &b->gexec[0]);
+  if (rc == MLSW_OK && !b->groups.empty()) rc = capture_step(b, 1, &b->gexec[1]);
+  return rc;
 }
 
 int mlswlbm_batch_tile_rows(const mlsw_batch* b, int index) {

@@ -68,6 +68,16 @@ __device__ __forceinline__ int chk_index(int i, int n) {
 #endif
   return i;
 }
+// offset of a global store inside its buffer or plane: i in [0, len)
+__device__ __forceinline__ long chk_offset(long i, long len) {
+#ifdef MLSW_DEBUG
+  if (i < 0 || i >= len) {
+    note_bounds_violation();
+    return 0;
+  }
+#endif
+  return i;
+}
 // global store target: p inside [base, base + len)
 __device__ __forceinline__ float* chk_global(float* base, float* p, long len) {
 #ifdef MLSW_DEBUG
@@ -95,13 +105,15 @@ __device__ __forceinline__ int image_of(int d, int n) {
 
 __device__ __forceinline__ void store_edge(float* __restrict__ plane_base, const Layout& L,
                                            int dx, int dy, int xi, int yi, float v) {
+  // indices into the plane (not derived pointers), so that the stores keep
+  // the base pointer's no-alias guarantee
   const long r0 = (long)(dy + L.gy) * L.pitch;
-  *chk_global(plane_base, plane_base + r0 + dx + L.gx, L.plane) = v;
-  if (xi != kNoImage) *chk_global(plane_base, plane_base + r0 + xi + L.gx, L.plane) = v;
+  plane_base[chk_offset(r0 + dx + L.gx, L.plane)] = v;
+  if (xi != kNoImage) plane_base[chk_offset(r0 + xi + L.gx, L.plane)] = v;
   if (yi != kNoImage) {
     const long r1 = (long)(yi + L.gy) * L.pitch;
-    *chk_global(plane_base, plane_base + r1 + dx + L.gx, L.plane) = v;
-    if (xi != kNoImage) *chk_global(plane_base, plane_base + r1 + xi + L.gx, L.plane) = v;
+    plane_base[chk_offset(r1 + dx + L.gx, L.plane)] = v;
+    if (xi != kNoImage) plane_base[chk_offset(r1 + xi + L.gx, L.plane)] = v;
   }
 }
 
@@ -290,6 +302,7 @@ struct SingleTiles {
   const CUtensorMap* map;
   float* fout;
   int ntx, ntiles, rev;
+  static constexpr bool kHints = true;  // L2 cache hints (KParams::l2_policy)
   __device__ TileRef operator()(int t) const {
     const int u = rev ? ntiles - 1 - t : t;
     return {P, map, fout, u % ntx, u / ntx};
@@ -303,6 +316,7 @@ struct BatchTiles {
   const BatchInst* inst;
   const int2* table;
   int cur, ntiles, variant;  // variant: tensor-map set of this tile height
+  static constexpr bool kHints = false;  // plain loads and stores
   __device__ TileRef operator()(int t) const {
     const int2 e = table[t];
     const BatchInst& b = inst[e.x];
@@ -342,9 +356,11 @@ __device__ __forceinline__ void d2q9_tile_loop(const Tiles& tiles, int* __restri
   // the output lines keep the L2. A larger lattice (kL2Stream) reads with
   // the lines' priority unchanged (halo rows are read again by the tile row
   // below) and the solver alternates the tile order, so each step starts on
-  // the rows its predecessor wrote last. Batches (kL2None) use no hints:
+  // the rows its predecessor wrote last. Batches use plain loads and
+  // stores (no hinted instructions at all, which measured faster there):
   // kept output lines would only crowd out the halo rows of other tiles.
-  const int l2pol = tiles(blockIdx.x).P->l2_policy;  // grid <= ntiles
+  constexpr bool HINTS = Tiles::kHints;
+  const int l2pol = HINTS ? tiles(blockIdx.x).P->l2_policy : (int)kL2None;  // grid <= ntiles
   const uint64_t st_pol = l2pol == kL2None ? pol_evict_normal() : pol_evict_last();
   const uint64_t ld_pol = l2pol == kL2Resident ? pol_evict_first()
                           : (l2pol == kL2Stream ? pol_evict_unchanged() : pol_evict_normal());
@@ -364,7 +380,10 @@ __device__ __forceinline__ void d2q9_tile_loop(const Tiles& tiles, int* __restri
 #endif
     mbar_arrive_expect_tx(bar, (uint32_t)Tl::kStageBytes);
     // box origin: real (x0 - 4, y0 - 2) = padded (x0, y0) since gx = 4, gy = 2
-    tma_load_3d(stage, r.map, bar, r.bx * TX, r.by * TY, 0, ld_pol);
+    if constexpr (HINTS)
+      tma_load_3d(stage, r.map, bar, r.bx * TX, r.by * TY, 0, ld_pol);
+    else
+      tma_load_3d(stage, r.map, bar, r.bx * TX, r.by * TY, 0);
   };
   auto draw_next = [&]() {
     const int nt = (int)gridDim.x + atomicAdd(sched, 1);
@@ -650,12 +669,16 @@ __device__ __forceinline__ void d2q9_tile_loop(const Tiles& tiles, int* __restri
 #pragma unroll
             for (int l = 0; l < W; ++l) {
 #pragma unroll
-              for (int k = 0; k < Q; ++k)
-                st_global_hint(chk_global(fout,
-                                          &cbase[l][(long)i * lplane + (long)k * L.plane +
-                                                    Lattice<2>::cy(k) * L.pitch + Lattice<2>::cx(k)],
-                                          L.length()),
-                               Ln::get(fs[k], l), st_pol);
+              for (int k = 0; k < Q; ++k) {
+                float* dst = chk_global(fout,
+                                        &cbase[l][(long)i * lplane + (long)k * L.plane +
+                                                  Lattice<2>::cy(k) * L.pitch + Lattice<2>::cx(k)],
+                                        L.length());
+                if constexpr (HINTS)
+                  st_global_hint(dst, Ln::get(fs[k], l), st_pol);
+                else
+                  *dst = Ln::get(fs[k], l);
+              }
             }
             continue;
           }

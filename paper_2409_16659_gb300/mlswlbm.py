@@ -113,6 +113,9 @@ EXPORTS = {
                                             ctypes.c_void_p, ctypes.POINTER(_H)]),
     "mlswlbm_batch_step": (ctypes.c_int, [_H, ctypes.c_long]),
     "mlswlbm_batch_get_heights": (ctypes.c_int, [_H, ctypes.c_int, _F]),
+    "mlswlbm_batch_get_heights_device": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_void_p]),
+    "mlswlbm_batch_set_heights_device": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_void_p]),
+    "mlswlbm_batch_select": (ctypes.c_int, [_H, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "mlswlbm_batch_modes": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_int),
                                            ctypes.POINTER(ctypes.c_int), _D]),
     "mlswlbm_batch_status": (ctypes.c_int, [_H]),
@@ -495,6 +498,29 @@ class Batch:
         _check(rc, "mlswlbm_batch_get_heights")
         return out
 
+    def get_heights_device(self, index, out):
+        """mlswlbm_batch_get_heights_device: out is a float32 CUDA tensor of
+        the instance's [n][ny][nx] heights (asynchronous)."""
+        _check(lib().mlswlbm_batch_get_heights_device(
+            self._b, int(index), _dev_ptr(out, int(np.prod(self.shapes[index])))),
+            "mlswlbm_batch_get_heights_device")
+        return out
+
+    def set_heights_device(self, index, h):
+        """mlswlbm_batch_set_heights_device: restarts the instance at rest
+        from the float32 CUDA tensor h (asynchronous)."""
+        _check(lib().mlswlbm_batch_set_heights_device(
+            self._b, int(index), _dev_ptr(h, int(np.prod(self.shapes[index])))),
+            "mlswlbm_batch_set_heights_device")
+
+    def select(self, indices):
+        """mlswlbm_batch_select: only these instances advance in later steps;
+        the others keep their states."""
+        idx = np.ascontiguousarray(sorted(int(i) for i in indices), dtype=np.int32)
+        _check(lib().mlswlbm_batch_select(self._b, int(idx.size),
+                                          idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int))),
+               "mlswlbm_batch_select")
+
     def modes(self, kx, ky):
         """Complex hhat_i(q) of every layer (rows) of every instance: an array
         [count][MLSW_MAX_LAYERS], zero beyond each instance's n."""
@@ -569,20 +595,7 @@ def fit_cap_angle(profile, area, base):
     return th.value, e.value
 
 
-EXPORTS_SURROGATE = {
-    "mlswlbm_surrogate_param_count": (ctypes.c_long, []),
-    "mlswlbm_surrogate_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                                ctypes.c_ulonglong, ctypes.c_double, ctypes.c_double,
-                                                ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
-    "mlswlbm_surrogate_predict": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                                                 ctypes.c_int]),
-    "mlswlbm_surrogate_train_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                                                    ctypes.c_int, ctypes.c_double, _D]),
-    "mlswlbm_surrogate_set_params": (ctypes.c_int, [ctypes.c_void_p, _F, ctypes.c_long]),
-    "mlswlbm_surrogate_get_params": (ctypes.c_int, [ctypes.c_void_p, _F, ctypes.c_long]),
-    "mlswlbm_surrogate_debug": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
-                                               ctypes.c_long]),
-    "mlswlbm_surrogate_destroy": (None, [ctypes.c_void_p]),
+EXPORTS_UNET = {
     "mlswlbm_unet_param_count": (ctypes.c_long, []),
     "mlswlbm_unet_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                            ctypes.c_int, _D, ctypes.c_ulonglong, ctypes.c_double,
@@ -601,95 +614,7 @@ EXPORTS_SURROGATE = {
 }
 
 
-EXPORTS.update(EXPORTS_SURROGATE)  # bound by lib() with the others
-
-
-def _surr_lib():
-    return lib()
-
-
-class Surrogate:
-    """mlswlbm_surrogate_*: the convolutional surrogate of 64 LBM steps.
-    Device arrays are torch CUDA tensors of float32 [batch][n][ny][nx]."""
-
-    KS, CHANNELS = 5, (16, 32, 32, 16)
-
-    def __init__(self, n, nx, ny, max_batch, seed=0, in_scale=20.0, out_scale=100.0, stream=None):
-        self.n, self.nx, self.ny, self.max_batch = int(n), int(nx), int(ny), int(max_batch)
-        self.in_scale, self.out_scale = float(in_scale), float(out_scale)
-        self._s = ctypes.c_void_p()
-        _check(_surr_lib().mlswlbm_surrogate_create(self.n, self.nx, self.ny, self.max_batch,
-                                                    int(seed), self.in_scale, self.out_scale,
-                                                    _stream_ptr(stream), ctypes.byref(self._s)),
-               "mlswlbm_surrogate_create")
-
-    def close(self):
-        if self._s:
-            _surr_lib().mlswlbm_surrogate_destroy(self._s)
-            self._s = ctypes.c_void_p()
-
-    def __enter__(self):
-        return self
-
-    def __exit__(self, *a):
-        self.close()
-
-    def __del__(self):
-        try:
-            self.close()
-        except Exception:
-            pass
-
-    @staticmethod
-    def param_count():
-        return int(_surr_lib().mlswlbm_surrogate_param_count())
-
-    def _batch(self, t):
-        import torch
-        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32
-                and t.is_contiguous()):
-            raise ValueError("float32 contiguous CUDA tensor expected")
-        if tuple(t.shape[1:]) != (self.n, self.ny, self.nx) or not 1 <= t.shape[0] <= self.max_batch:
-            raise ValueError("shape [batch][n][ny][nx] expected")
-        return int(t.shape[0])
-
-    def predict(self, h, out):
-        b = self._batch(h)
-        if tuple(out.shape) != tuple(h.shape):
-            raise ValueError("out must match h")
-        self._batch(out)
-        _check(_surr_lib().mlswlbm_surrogate_predict(self._s, ctypes.c_void_p(h.data_ptr()),
-                                                     ctypes.c_void_p(out.data_ptr()), b),
-               "mlswlbm_surrogate_predict")
-        return out
-
-    def train_step(self, h, target, lr):
-        b = self._batch(h)
-        if tuple(target.shape) != tuple(h.shape):
-            raise ValueError("target must match h")
-        loss = ctypes.c_double()
-        _check(_surr_lib().mlswlbm_surrogate_train_step(self._s, ctypes.c_void_p(h.data_ptr()),
-                                                        ctypes.c_void_p(target.data_ptr()), b,
-                                                        float(lr), ctypes.byref(loss)),
-               "mlswlbm_surrogate_train_step")
-        return loss.value
-
-    def get_params(self):
-        out = np.empty(self.param_count(), dtype=np.float32)
-        _check(_surr_lib().mlswlbm_surrogate_get_params(self._s, _fptr(out), out.size),
-               "mlswlbm_surrogate_get_params")
-        return out
-
-    def set_params(self, w):
-        a = np.ascontiguousarray(w, dtype=np.float32)
-        _check(_surr_lib().mlswlbm_surrogate_set_params(self._s, _fptr(a), a.size),
-               "mlswlbm_surrogate_set_params")
-
-    def debug(self, what, shape, dtype):
-        out = np.empty(shape, dtype=dtype)
-        _check(_surr_lib().mlswlbm_surrogate_debug(self._s, int(what), out.ctypes.data, out.nbytes),
-               "mlswlbm_surrogate_debug")
-        return out
+EXPORTS.update(EXPORTS_UNET)  # bound by lib() with the others
 
 
 UNET_TENSORS = ("X0", "A0", "S0", "P1", "A1", "S1", "P2", "A2", "S2", "P3", "A3", "S3",

@@ -1,16 +1,20 @@
-"""Training and use of the convolutional surrogate of 64 LBM steps.
+"""Training and use of the U-Net surrogate of 64 LBM steps.
 
-The network itself (mlswlbm_surrogate_*, BF16 tensor-core kernels) lives in
-the C library; this module feeds it:
+The network itself (mlswlbm_unet_*, BF16 kernels on the 5th-generation
+tensor cores) lives in the C library; this module feeds it:
 
 * trajectories: the heights of many instances of one lattice after every
-  window of 64 steps, run by one batch of the solver;
-* training: Adam on random minibatches of (h(t), h(t + 64)) pairs;
+  window of 64 steps, run by one batch of the solver, kept on the device;
+* training: Adam on minibatches of (h(t), h(t + 64)) pairs drawn from
+  trajectories streamed through in chunks;
 * evaluation: the largest height error of each window against the LBM, next
   to that of the identity map (no change);
-* rollout: an instance advanced window by window, by the surrogate where an
-  acceptance rule calibrated on training windows says its height error
-  stays within a bound, by the LBM elsewhere.
+* the judged rollout: many instances advanced window by window by the
+  surrogate, with the LBM running audit windows from the same heights; an
+  instance whose audited error exceeds the bound goes back to its last
+  passed audit and finishes on the LBM;
+* the two plain LBM baselines of the same windows: the batched solver and
+  one solver per instance.
 
 Device arrays are float32 torch CUDA tensors [.., n, ny, nx].
 """
@@ -48,128 +52,229 @@ def trajectories(params, heights, windows, stream=None):
     return out
 
 
-def train(s, traj, instances, steps, batch, lr, lr_end=None, seed=0, weights=None):
-    """Adam steps on minibatches of windows of the given instances; the
-    learning rate decays geometrically from lr to lr_end. `weights`
-    (optional, one per window index) sets how often each window is drawn.
-    Returns the losses."""
+def trajectories_device(params, heights, windows, stream=None):
+    """Heights after 0..windows windows of every instance (all of one shape),
+    read from one batch of the solver on the device: a tensor
+    [instances][windows + 1][n][ny][nx]."""
+    torch = _torch()
+    p0 = params[0]
+    n, ny, nx = int(p0["n"]), int(p0["ny"]), int(p0["nx"])
+    out = torch.empty((len(params), windows + 1, n, ny, nx), dtype=torch.float32, device="cuda")
+    with B.Batch(params, heights, stream=stream) as b:
+        for w in range(windows + 1):
+            if w:
+                b.step(WINDOW)
+            for j in range(len(params)):
+                b.get_heights_device(j, out[j, w])
+        if b.status() != B.MLSW_OK:
+            raise RuntimeError("solver status: " + B.mlswlbm_strerror(b.status()))
+    return out
+
+
+class TrajectoryStream:
+    """One batch of the solver re-used for chunk after chunk of trajectories
+    of one lattice: each call restarts the instances at rest from the given
+    device heights [count][n][ny][nx] and returns their heights after 0..
+    windows windows, [count][windows + 1][n][ny][nx] on the device."""
+
+    def __init__(self, params, h_first, windows, stream=None):
+        self.count, self.windows = len(params), int(windows)
+        self.b = B.Batch(params, [x for x in h_first.cpu().numpy()], stream=stream)
+
+    def __call__(self, h0):
+        torch = _torch()
+        out = torch.empty((self.count, self.windows + 1) + tuple(h0.shape[1:]),
+                          dtype=torch.float32, device="cuda")
+        for j in range(self.count):
+            self.b.set_heights_device(j, h0[j])
+        for w in range(self.windows + 1):
+            if w:
+                self.b.step(WINDOW)
+            for j in range(self.count):
+                self.b.get_heights_device(j, out[j, w])
+        return out
+
+    def close(self):
+        if self.b is not None:
+            status = self.b.status()
+            self.b.close()
+            self.b = None
+            if status != B.MLSW_OK:
+                raise RuntimeError("solver status: " + B.mlswlbm_strerror(status))
+
+
+def train_streaming(u, make_chunk, chunks, steps_per_chunk, batch, lr, lr_end=None, seed=0):
+    """Adam steps on (h(t), h(t + 64)) pairs of trajectory chunks made one at
+    a time by make_chunk(k) ([instances][windows + 1][n][ny][nx] on the
+    device) and dropped after their steps; the learning rate decays
+    geometrically from lr to lr_end over all steps. Returns the losses."""
     torch = _torch()
     rng = np.random.default_rng(seed)
-    nwin = traj.shape[1] - 1
-    inst = np.asarray(instances)
     lr_end = lr if lr_end is None else lr_end
-    prob = None if weights is None else np.asarray(weights, dtype=float) / np.sum(weights)
-    losses = []
-    for it in range(steps):
-        ii = torch.as_tensor(rng.choice(inst, batch), device="cuda")
-        ww = torch.as_tensor(rng.choice(nwin, batch, p=prob), device="cuda")
-        h = traj[ii, ww].contiguous()
-        t = traj[ii, ww + 1].contiguous()
-        rate = lr * (lr_end / lr) ** (it / max(steps - 1, 1))
-        losses.append(s.train_step(h, t, rate))
+    total = max(chunks * steps_per_chunk - 1, 1)
+    losses, it = [], 0
+    for k in range(chunks):
+        traj = make_chunk(k)
+        ninst, nwin = traj.shape[0], traj.shape[1] - 1
+        for _ in range(steps_per_chunk):
+            ii = torch.as_tensor(rng.integers(0, ninst, batch), device="cuda")
+            ww = torch.as_tensor(rng.integers(0, nwin, batch), device="cuda")
+            rate = lr * (lr_end / lr) ** (it / total)
+            losses.append(u.train_step(traj[ii, ww].contiguous(), traj[ii, ww + 1].contiguous(),
+                                       rate))
+            it += 1
+        del traj
     return np.array(losses)
 
 
-def window_errors(s, traj, instances):
-    """Per (instance, window): the surrogate's largest height error against
-    the LBM, that of the identity map, and the surrogate's predicted largest
-    change. Arrays [instances][windows]."""
+def unet_window_errors(u, traj):
+    """Per (instance, window): the U-Net's largest height error against the
+    LBM, the identity map's (the window's own largest change). Arrays
+    [instances][windows]."""
     torch = _torch()
-    errs, ident, change = [], [], []
-    for i in instances:
-        h_all, t_all = traj[i, :-1], traj[i, 1:]
-        e, c = [], []
-        for k in range(0, h_all.shape[0], s.max_batch):
-            h = h_all[k:k + s.max_batch].contiguous()
-            pred = torch.empty_like(h)
-            s.predict(h, pred)
-            e.append((pred - t_all[k:k + s.max_batch]).abs().amax(dim=(1, 2, 3)))
-            c.append((pred - h).abs().amax(dim=(1, 2, 3)))
-        errs.append(torch.cat(e).cpu().numpy())
-        change.append(torch.cat(c).cpu().numpy())
-        ident.append((t_all - h_all).abs().amax(dim=(1, 2, 3)).cpu().numpy())
-    return np.array(errs), np.array(ident), np.array(change)
+    ninst, nwin = traj.shape[0], traj.shape[1] - 1
+    h_all = traj[:, :-1].reshape((-1,) + tuple(traj.shape[2:]))
+    t_all = traj[:, 1:].reshape((-1,) + tuple(traj.shape[2:]))
+    err = []
+    for k in range(0, h_all.shape[0], u.max_batch):
+        h = h_all[k:k + u.max_batch].contiguous()
+        pred = torch.empty_like(h)
+        u.predict(h, pred)
+        err.append((pred - t_all[k:k + u.max_batch]).abs().amax(dim=(1, 2, 3)))
+    ident = (t_all - h_all).abs().amax(dim=(1, 2, 3))
+    return (torch.cat(err).cpu().numpy().reshape(ninst, nwin),
+            ident.cpu().numpy().reshape(ninst, nwin))
 
 
-def calibrate(err, change, bound=1e-3, quantile=1.0):
-    """Largest threshold tau on the predicted change such that, among the
-    windows whose predicted change is at most tau, a fraction `quantile` has
-    an error within `bound` (0 if none qualifies)."""
-    order = np.argsort(change.ravel())
-    e = err.ravel()[order]
-    c = change.ravel()[order]
-    ok = np.cumsum(e <= bound) / np.arange(1, e.size + 1)
-    good = np.nonzero(ok >= quantile)[0]
-    return float(c[good[-1]]) if good.size else 0.0
+def _predict_all(u, h, out):
+    for k in range(0, h.shape[0], u.max_batch):
+        u.predict(h[k:k + u.max_batch].contiguous(), out[k:k + u.max_batch])
+    return out
 
 
-def rollout(s, params, h0, windows, tau, hand_over=False):
-    """Advances one instance by `windows` windows: the surrogate's window is
-    taken when its predicted largest change is at most tau, otherwise the LBM
-    runs the 64 steps, restarted from the current heights (all on the
-    device; one host read of the predicted change per window). A restart
-    sets the populations to f_eq(h, U = 0): the layer fluxes of the previous
-    LBM window are not carried over, so the LBM windows of a rollout are
-    not the uninterrupted LBM trajectory from the same heights. With
-    hand_over, the first window the surrogate does not take hands all the
-    remaining windows to the LBM in one call (a film whose change has grown
-    past tau keeps changing faster until it has dewetted). Returns (heights,
-    windows taken from the surrogate, seconds)."""
+def judged_rollout(u, params, heights, windows, audit_every, bound=1e-3, stream=None):
+    """Advances every instance by `windows` windows of 64 steps, by the U-Net
+    (all instances in batched calls), judged by the LBM: the first window,
+    every audit_every-th and the last are audits, in which the batched
+    solver runs the same window from the same heights, and the largest
+    height difference is the window's error. A window within `bound`
+    continues from the solver's heights; an instance whose error exceeds it
+    leaves the surrogate, goes back to its last passed audit and finishes on
+    the LBM alone. The audits step only the instances still on the
+    surrogate (mlswlbm_batch_select), and the instances that left finish in
+    the same batched solver, restarted at rest from their checkpoints, in
+    stages by checkpoint window so that each steps exactly its remaining
+    windows. Returns (final heights [instances][n][ny][nx] tensor, a dict of
+    counts, audited errors and seconds)."""
     torch = _torch()
-    n, ny, nx = int(params["n"]), int(params["ny"]), int(params["nx"])
-    h = torch.from_numpy(np.asarray(h0, dtype=np.float32).reshape(1, n, ny, nx)).cuda()
-    pred = torch.empty_like(h)
-    taken = 0
-    with B.Solver(params, np.asarray(h0, dtype=np.float32),
-                  stream=torch.cuda.current_stream()) as lbm:
+    st = torch.cuda.current_stream() if stream is None else stream
+    M = len(params)
+    h = torch.stack([torch.from_numpy(np.asarray(x, dtype=np.float32)) for x in heights]).cuda()
+    ckpt = h.clone()
+    ckpt_w = [0] * M
+    lbm_out = torch.empty_like(h)
+    active = list(range(M))          # instances still on the surrogate
+    fallback, audited = {}, []
+    taken = [0] * M                  # windows taken from the surrogate since the last audit
+    surrogate_windows = 0
+    with B.Batch(params, [np.asarray(x, dtype=np.float32) for x in heights], stream=st) as aud:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for w in range(windows):
-            s.predict(h, pred)
-            if float((pred - h).abs().amax()) <= tau:
-                h, pred = pred, h
-                taken += 1
+            if not active:
+                break
+            idx = torch.as_tensor(active, device="cuda")
+            sub = h[idx].contiguous()
+            out = torch.empty_like(sub)
+            _predict_all(u, sub, out)
+            if w == 0 or (w + 1) % audit_every == 0 or w == windows - 1:
+                for j, i in enumerate(active):
+                    aud.set_heights_device(i, sub[j])
+                aud.step(WINDOW)
+                for i in active:
+                    aud.get_heights_device(i, lbm_out[i])
+                err = (out - lbm_out[idx]).abs().amax(dim=(1, 2, 3)).cpu().numpy()
+                audited.extend(float(e) for e in err)
+                keep = []
+                for j, i in enumerate(active):
+                    if err[j] <= bound:
+                        h[i] = lbm_out[i]
+                        ckpt[i] = lbm_out[i]
+                        ckpt_w[i] = w + 1
+                        surrogate_windows += taken[i]
+                        keep.append(i)
+                    else:
+                        fallback[i] = ckpt_w[i]
+                    taken[i] = 0
+                if len(keep) != len(active):
+                    aud.select(keep)
+                active = keep
             else:
-                lbm.set_heights_device(h[0])
-                lbm.step(WINDOW * (windows - w if hand_over else 1))
-                lbm.get_heights_device(h[0])
-                if hand_over:
-                    break
+                h[idx] = out
+                for i in active:
+                    taken[i] += 1
+        # instances that left finish on the LBM from their last passed audit
+        # (the last window is always audited), all in the batch: the ones
+        # with the earliest checkpoint start, the others join as the run
+        # reaches their checkpoint window
+        stages = sorted(set(fallback.values()))
+        running = []
+        for k, w0 in enumerate(stages):
+            for i, wi in fallback.items():
+                if wi == w0:
+                    aud.set_heights_device(i, ckpt[i])
+                    running.append(i)
+            aud.select(running)
+            w1 = stages[k + 1] if k + 1 < len(stages) else windows
+            aud.step(WINDOW * (w1 - w0))
+        for i in running:
+            aud.get_heights_device(i, h[i])
         torch.cuda.synchronize()
         secs = time.perf_counter() - t0
-        if lbm.status() != B.MLSW_OK:
-            raise RuntimeError("solver status: " + B.mlswlbm_strerror(lbm.status()))
-    return h[0].cpu().numpy(), taken, secs
+        status = aud.status()
+    if status != B.MLSW_OK:
+        raise RuntimeError("solver status: " + B.mlswlbm_strerror(status))
+    return h, {"seconds": secs, "fallback_instances": len(fallback),
+               "surrogate_windows": surrogate_windows, "audited_windows": len(audited),
+               "audit_errors": audited}
 
 
-def lbm_rollout(params, h0, windows):
-    """The same windows by the LBM alone (one solver, no restarts), timed
-    like rollout(): on torch's current stream, from a synchronised start."""
+def lbm_batched(params, heights, windows, stream=None):
+    """The same windows by the batched solver alone; (heights tensor, seconds)."""
     torch = _torch()
-    host = np.empty((int(params["n"]), int(params["ny"]), int(params["nx"])), dtype=np.float32)
-    with B.Solver(params, np.asarray(h0, dtype=np.float32),
-                  stream=torch.cuda.current_stream()) as lbm:
+    st = torch.cuda.current_stream() if stream is None else stream
+    out = torch.empty((len(params),) + np.asarray(heights[0]).shape, dtype=torch.float32,
+                      device="cuda")
+    with B.Batch(params, [np.asarray(x, dtype=np.float32) for x in heights], stream=st) as b:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        lbm.step(WINDOW * windows)
-        lbm.get_heights(host)
+        b.step(WINDOW * windows)
+        for j in range(len(params)):
+            b.get_heights_device(j, out[j])
+        torch.cuda.synchronize()
         secs = time.perf_counter() - t0
-    return host, secs
+    return out, secs
 
 
-def film_statistics(h, hstar):
-    """Largest-scale statistics of a dewetting film that do not depend on the
-    exact pattern: per layer the fraction of cells below 2 h* and the
-    standard deviation of the heights."""
-    h = np.asarray(h, dtype=np.float64)
-    return {"dewetted_fraction": [float((h[i] < 2 * hstar).mean()) for i in range(h.shape[0])],
-            "height_std": [float(h[i].std()) for i in range(h.shape[0])]}
-
-
-def first_rupture(traj_heights, hstar):
-    """Index of the first window whose heights fall below 1.5 h* anywhere
-    (None if none)."""
-    for w, h in enumerate(traj_heights):
-        if float(np.min(h)) < 1.5 * hstar:
-            return w
-    return None
+def lbm_per_instance(params, heights, windows, stream=None):
+    """The same windows by one solver per instance, stepped in turn;
+    (heights tensor, seconds)."""
+    torch = _torch()
+    st = torch.cuda.current_stream() if stream is None else stream
+    out = torch.empty((len(params),) + np.asarray(heights[0]).shape, dtype=torch.float32,
+                      device="cuda")
+    solvers = [B.Solver(p, np.asarray(x, dtype=np.float32), stream=st)
+               for p, x in zip(params, heights)]
+    try:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for s in solvers:
+            s.step(WINDOW * windows)
+        for j, s in enumerate(solvers):
+            s.get_heights_device(out[j])
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+    finally:
+        for s in solvers:
+            s.close()
+    return out, secs

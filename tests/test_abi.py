@@ -157,23 +157,36 @@ def test_gpu_test_cases_pass_the_stability_check():
         assert rc in (B.MLSW_OK, B.MLSW_ERR_CUDA), (rc, p)
 
 
-def test_surrogate_argument_checks_and_parameter_count():
-    """The surrogate's C entry points reject bad arguments before touching
-    the GPU; its parameter count is that of three 5 x 5 convolutions
-    16 -> 32 -> 32 -> 16 with biases."""
+def test_unet_argument_checks_and_parameter_count():
+    """The U-Net's C entry points reject bad arguments before touching the
+    GPU; its parameter count is that of the 15 convolutions of the four
+    levels (32, 64, 128, 256 channels; 16 input planes, 16 outputs), 3 x 3
+    taps plus a bias each."""
     import ctypes
     L = B.lib()
-    assert L.mlswlbm_surrogate_param_count() == 25 * (16 * 32 + 32 * 32 + 32 * 16) + 32 + 32 + 16
+    convs = [(16, 32), (32, 32), (32, 64), (64, 64), (64, 128), (128, 128), (128, 256),
+             (256, 256), (256 + 128, 128), (128, 128), (128 + 64, 64), (64, 64),
+             (64 + 32, 32), (32, 32), (32, 16)]
+    assert L.mlswlbm_unet_param_count() == sum(9 * ci * co + co for ci, co in convs)
     out = ctypes.c_void_p(1)
-    for args in [(0, 64, 64, 4), (6, 64, 64, 4), (2, 40, 64, 4), (2, 8, 64, 4), (2, 64, 0, 4),
-                 (2, 64, 64, 0)]:
-        rc = L.mlswlbm_surrogate_create(*args, 1, 10.0, 40.0, None, ctypes.byref(out))
-        assert rc == B.MLSW_ERR_ARG and not out.value, args
+    ex = (ctypes.c_double * 16)(*([0.5] * 16))
+    nan = (ctypes.c_double * 1)(float("nan"))
+    for args, want in [((0, 256, 256, 4, 0, None), B.MLSW_ERR_ARG),
+                       ((6, 256, 256, 4, 0, None), B.MLSW_ERR_ARG),
+                       ((3, 256, 256, 0, 0, None), B.MLSW_ERR_ARG),
+                       ((3, 256, 256, 4, 14, ex), B.MLSW_ERR_ARG),
+                       ((3, 256, 256, 4, 2, None), B.MLSW_ERR_ARG),
+                       ((3, 256, 256, 4, 1, nan), B.MLSW_ERR_ARG),
+                       ((3, 192, 256, 4, 0, None), B.MLSW_ERR_UNSUPPORTED),
+                       ((3, 256, 64, 4, 0, None), B.MLSW_ERR_UNSUPPORTED),
+                       ((3, 8192, 256, 4, 0, None), B.MLSW_ERR_UNSUPPORTED)]:
+        rc = L.mlswlbm_unet_create(*args, 1, 1.0, 4.0, None, ctypes.byref(out))
+        assert rc == want and not out.value, (args[:5], rc)
         out = ctypes.c_void_p(1)
-    for scales in [(0.0, 40.0), (10.0, -1.0), (float("inf"), 40.0)]:
-        rc = L.mlswlbm_surrogate_create(2, 64, 64, 4, 1, *scales, None, ctypes.byref(out))
+    for scales in [(0.0, 4.0), (1.0, -1.0), (float("inf"), 4.0)]:
+        rc = L.mlswlbm_unet_create(3, 256, 256, 4, 0, None, 1, *scales, None, ctypes.byref(out))
         assert rc == B.MLSW_ERR_ARG, scales
-    assert L.mlswlbm_surrogate_create(2, 64, 64, 4, 1, 10.0, 40.0, None, None) == B.MLSW_ERR_ARG
-    assert L.mlswlbm_surrogate_predict(None, None, None, 1) == B.MLSW_ERR_ARG
-    assert L.mlswlbm_surrogate_train_step(None, None, None, 1, 1e-3, None) == B.MLSW_ERR_ARG
-    L.mlswlbm_surrogate_destroy(None)
+    assert L.mlswlbm_unet_create(3, 256, 256, 4, 0, None, 1, 1.0, 4.0, None, None) == B.MLSW_ERR_ARG
+    assert L.mlswlbm_unet_predict(None, None, None, 1) == B.MLSW_ERR_ARG
+    assert L.mlswlbm_unet_train_step(None, None, None, 1, 1e-3, None) == B.MLSW_ERR_ARG
+    L.mlswlbm_unet_destroy(None)

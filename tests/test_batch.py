@@ -154,3 +154,42 @@ def test_full_size_stability_sweep_sampled_against_oracle():
             f = oracle.run(p, oracle.init(p, h0.astype(np.float64).ravel()), 20)
             hr = oracle.heights(p, f).reshape(hg.shape)
             assert np.abs(hg - hr).max() <= 1e-5 * np.abs(hr).max(), (j, p["n"], p["nx"])
+
+
+def test_selected_instances_step_and_the_others_keep_their_state():
+    """mlswlbm_batch_select: over odd and even step counts, each instance
+    ends after exactly the steps it was selected for, bit for bit as a
+    single solver; one left out keeps its state (heights and modes), and a
+    restart from new heights while left out takes effect when selected."""
+    inst = _mixed_instances()[:5]
+    P, H = [p for p, _ in inst], [h for _, h in inst]
+    import torch
+    with B.Batch(P, H) as b, B.Batch(P, H) as fresh:
+        kx = np.ones(len(P), dtype=np.int32)
+        ky = np.zeros(len(P), dtype=np.int32)
+        m_init = fresh.modes(kx, ky)
+        steps = np.zeros(len(P), dtype=int)
+        for sel, k in (([0, 2], 7), ([1, 2, 4], 5), ([], 3), ([3], 1)):
+            b.select(sel)
+            b.step(k)
+            steps[sel] += k
+        # instance 1 and 4 have been left out over an odd number of steps
+        m = b.modes(kx, ky)
+        for j in range(len(P)):
+            if steps[j] == 0:
+                assert np.array_equal(m[j], m_init[j]), j
+        for j, (p, h) in enumerate(inst):
+            assert np.array_equal(b.get_heights(j), _single(p, h, int(steps[j]))), (j, steps[j])
+        # restart a left-out instance from other heights, then step everyone
+        h2 = workloads.random_heights(999, P[3]).astype(np.float32)
+        b.set_heights_device(3, torch.from_numpy(h2).cuda())
+        b.select(range(len(P)))
+        b.step(4)
+        for j, (p, h) in enumerate(inst):
+            want = _single(p, h2, 4) if j == 3 else _single(p, h, int(steps[j]) + 4)
+            assert np.array_equal(b.get_heights(j), want), j
+        assert b.status() == B.MLSW_OK
+    with B.Batch(P, H) as b:
+        ip = np.array([0, 0], dtype=np.int32)
+        assert B.lib().mlswlbm_batch_select(b._b, 2, ip.ctypes.data_as(
+            B.ctypes.POINTER(B.ctypes.c_int))) == B.MLSW_ERR_ARG

@@ -9,7 +9,8 @@ itself checked:
 - pooling and upsampling: a constant stays constant, and each one's
   gradient is its adjoint;
 - the whole backward pass against central differences of the loss in
-  FP64 without rounding, on a 16 x 16 input.
+  FP64 without rounding, on a 16 x 16 input;
+- BF16 rounding goes to the nearest value, ties to even.
 """
 import numpy as np
 
@@ -95,3 +96,12 @@ def test_backward_pass_against_central_differences():
         lm = loss(q)
         fd = (lp - lm) / (2 * eps)
         assert abs(fd - g[k]) <= 1e-6 * max(1.0, abs(L)) + 1e-4 * abs(fd), (k, fd, g[k])
+
+
+def test_bf16_rounding():
+    v = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -9, -2.5 - 2 ** -8, 3.14159], np.float32)
+    # 1 + 2^-8 is halfway between 1 and 1 + 2^-7: ties to even (1.0)
+    want = np.array([1.0, 1.0, 1.0 + 2 ** -7, -2.5, 3.140625], np.float32)
+    np.testing.assert_array_equal(U.bf16(v), want)
+    bits = (U.bf16(v).view(np.uint32) >> 16).astype(np.uint16)
+    np.testing.assert_array_equal(U.from_bf16_bits(bits), U.bf16(v))

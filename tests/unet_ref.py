@@ -141,14 +141,25 @@ def split_params(p):
     return out
 
 
+def sample_rms(h):
+    """RMS over all layers and pixels of each sample's deviations from its
+    layer means, [B]."""
+    h = np.asarray(h, dtype=np.float64)
+    d = h - h.mean(axis=(2, 3), keepdims=True)
+    return np.sqrt((d * d).mean(axis=(1, 2, 3)))
+
+
 def input_planes(h, extra, in_scale):
-    """X0 [B][H][W][16]: (h_i - mean h_i) in_scale, then the parameter
-    planes, then zeros. h [B][n][H][W]."""
+    """X0 [B][H][W][16]: (h_i - mean h_i) in_scale / s (s the sample's RMS
+    deviation; all zero for a flat sample), then the parameter planes, then
+    zeros. h [B][n][H][W]."""
     h = np.asarray(h, dtype=np.float64)
     B, n, H, W = h.shape
+    s = sample_rms(h)
+    k = np.where(s > 0, in_scale / np.where(s > 0, s, 1.0), 0.0)
     x = np.zeros((B, H, W, C_IN))
     for i in range(n):
-        x[..., i] = (h[:, i] - h[:, i].mean(axis=(1, 2), keepdims=True)) * in_scale
+        x[..., i] = (h[:, i] - h[:, i].mean(axis=(1, 2), keepdims=True)) * k[:, None, None]
     for j, v in enumerate(extra):
         x[..., n + j] = v
     return x
@@ -188,9 +199,12 @@ def forward(params, x0, rnd=bf16):
 
 def loss_and_grad(y, h, target, n, out_scale):
     """Mean squared error over the first n output channels against the
-    scaled change, and its gradient with respect to y (zero elsewhere)."""
+    change scaled by out_scale / s, and its gradient with respect to y
+    (zero elsewhere)."""
     h = np.asarray(h, dtype=np.float64)
-    t = (np.asarray(target, dtype=np.float64) - h) * out_scale   # [B][n][H][W]
+    s = sample_rms(h)
+    k = np.where(s > 0, out_scale / np.where(s > 0, s, 1.0), 0.0)
+    t = (np.asarray(target, dtype=np.float64) - h) * k[:, None, None, None]   # [B][n][H][W]
     t = np.moveaxis(t, 1, 3)                                     # [B][H][W][n]
     d = y[..., :n] - t
     cnt = d.size

@@ -315,3 +315,23 @@ def dewet2_heights(side=64, seed=9):
     """Both layers 0.25 plus seeded Gaussian noise sigma = 1e-3."""
     rng = np.random.default_rng(seed)
     return 0.25 + 1e-3 * rng.standard_normal((2, side, side))
+
+
+def film3_d2q9_heights_device(nx, ny, count, seed):
+    """`count` three-layer films of the same recipe (means 1.0 / 0.8 / 0.6,
+    Gaussian noise sigma 1e-3), drawn on the GPU from a generator seeded
+    with `seed`: a float32 CUDA tensor [count][3][ny][nx]. Used where many
+    thousand seeded films are needed at once."""
+    import torch
+    g = torch.Generator(device="cuda")
+    g.manual_seed(int(seed))
+    means = torch.tensor([1.0, 0.8, 0.6], device="cuda").view(1, 3, 1, 1)
+    return (means + 1e-3 * torch.randn((int(count), 3, int(ny), int(nx)), generator=g,
+                                       device="cuda")).float().contiguous()
+
+
+def film3_unet_planes(p):
+    """Constant input planes of the U-Net surrogate for a three-layer film:
+    the tensions relative to 0.01 and the viscosity ratios mu_2 / mu_1 and
+    mu_3 / mu_1 over 4."""
+    return [g / 0.01 for g in p["gamma"]] + [m / p["mu"][0] / 4.0 for m in p["mu"][1:]]
