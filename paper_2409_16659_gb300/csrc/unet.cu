@@ -451,118 +451,189 @@ __device__ __forceinline__ float2 ld_pair(const bf16* t, long off) {
   return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(t + off));
 }
 
-// dst (H/2 x W/2) = 2 x 2 mean of src (H x W), C channels
-__global__ void pool_kernel(const bf16* __restrict__ src, bf16* __restrict__ dst, int B, int H, int W,
-                            int C) {
-  const int h2 = H / 2, w2 = W / 2, cp = C / 2;
-  const long total = (long)B * h2 * w2 * cp;
+// ---------------------------------------------------------------------------
+// Pooling, upsampling and their gradients work on 8-channel groups (16
+// bytes): a thread takes one group of one output pixel. Tensor sides are
+// powers of two (lgW = log2 W), channel counts multiples of 8.
+// ---------------------------------------------------------------------------
+struct Oct {
+  float v[8];
+};
+__device__ __forceinline__ Oct ld_oct(const bf16* t, long off) {
+  const uint4 q = *reinterpret_cast<const uint4*>(t + off);
+  const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+  Oct o;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[j]));
+    o.v[2 * j] = f.x;
+    o.v[2 * j + 1] = f.y;
+  }
+  return o;
+}
+// one pixel's 8 channels c .. c + 7 and their periodic images
+__device__ __forceinline__ void st_oct(bf16* t, int b, int y, int x, int H, int W, int C, int c,
+                                       const Oct& o) {
+  uint4 q;
+  uint32_t* w = reinterpret_cast<uint32_t*>(&q);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    __nv_bfloat162 h2 = __floats2bfloat162_rn(o.v[2 * j], o.v[2 * j + 1]);
+    w[j] = *reinterpret_cast<uint32_t*>(&h2);
+  }
+  const int xs[2] = {x + 1, x == 0 ? W + 1 : (x == W - 1 ? 0 : -1)};
+  const int ys[2] = {y + 1, y == 0 ? H + 1 : (y == H - 1 ? 0 : -1)};
+#pragma unroll
+  for (int iy = 0; iy < 2; ++iy)
+#pragma unroll
+    for (int ix = 0; ix < 2; ++ix)
+      if (ys[iy] >= 0 && xs[ix] >= 0)
+        *reinterpret_cast<uint4*>(t + (((long)b * (H + 2) + ys[iy]) * (W + 2) + xs[ix]) * C + c) = q;
+}
+// work item i of a (B x H x W pixels) x (C / 8 groups) loop
+struct OctIdx {
+  int b, y, x, c;
+};
+__device__ __forceinline__ OctIdx oct_idx(long i, int lgH, int lgW, int lgG) {
+  OctIdx r;
+  r.c = (int)(i & ((1 << lgG) - 1)) * 8;
+  const long p = i >> lgG;
+  r.x = (int)(p & ((1 << lgW) - 1));
+  r.y = (int)((p >> lgW) & ((1 << lgH) - 1));
+  r.b = (int)(p >> (lgW + lgH));
+  return r;
+}
+
+// dst (H/2 x W/2, lgH, lgW its sides) = 2 x 2 mean of src (H x W)
+__global__ void pool_kernel(const bf16* __restrict__ src, bf16* __restrict__ dst, int B, int lgH,
+                            int lgW, int lgG) {
+  const int H = 1 << lgH, W = 1 << lgW, C = 8 << lgG;
+  const long total = (long)B << (lgH + lgW + lgG);
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
-    const int c = (int)(i % cp) * 2;
-    long r = i / cp;
-    const int x = (int)(r % w2);
-    r /= w2;
-    const int y = (int)(r % h2), b = (int)(r / h2);
-    float2 s = make_float2(0.f, 0.f);
+    const OctIdx k = oct_idx(i, lgH, lgW, lgG);
+    Oct s = {};
     for (int q = 0; q < 4; ++q) {
-      const float2 v = ld_pair(src, hidx(b, 2 * y + q / 2, 2 * x + q % 2, H, W, C) + c);
-      s.x += v.x;
-      s.y += v.y;
+      const Oct v = ld_oct(src, hidx(k.b, 2 * k.y + q / 2, 2 * k.x + q % 2, 2 * H, 2 * W, C) + k.c);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) s.v[j] += v.v[j];
     }
-    st_pair(dst, b, y, x, h2, w2, C, c, 0.25f * s.x, 0.25f * s.y);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s.v[j] *= 0.25f;
+    st_oct(dst, k.b, k.y, k.x, H, W, C, k.c, s);
   }
 }
 
 // dst (H x W) = nearest 2x upsampling of src (H/2 x W/2)
-__global__ void up_kernel(const bf16* __restrict__ src, bf16* __restrict__ dst, int B, int H, int W,
-                          int C) {
-  const int cp = C / 2;
-  const long total = (long)B * H * W * cp;
+__global__ void up_kernel(const bf16* __restrict__ src, bf16* __restrict__ dst, int B, int lgH,
+                          int lgW, int lgG) {
+  const int H = 1 << lgH, W = 1 << lgW, C = 8 << lgG;
+  const long total = (long)B << (lgH + lgW + lgG);
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
-    const int c = (int)(i % cp) * 2;
-    long r = i / cp;
-    const int x = (int)(r % W);
-    r /= W;
-    const int y = (int)(r % H), b = (int)(r / H);
-    const float2 v = ld_pair(src, hidx(b, y / 2, x / 2, H / 2, W / 2, C) + c);
-    st_pair(dst, b, y, x, H, W, C, c, v.x, v.y);
+    const OctIdx k = oct_idx(i, lgH, lgW, lgG);
+    st_oct(dst, k.b, k.y, k.x, H, W, C, k.c, ld_oct(src, hidx(k.b, k.y / 2, k.x / 2, H / 2, W / 2, C) + k.c));
   }
 }
 
-// dS (H/2 x W/2) = (sum of the 2 x 2 fine pixels of dU) * (S > 0)
+// dS (H/2 x W/2, the sides given) = (sum of the 2 x 2 fine pixels of dU) * (S > 0)
 __global__ void up_grad_mask_kernel(const bf16* __restrict__ dU, const bf16* __restrict__ Sact,
-                                    bf16* __restrict__ dS, int B, int H, int W, int C) {
-  const int h2 = H / 2, w2 = W / 2, cp = C / 2;
-  const long total = (long)B * h2 * w2 * cp;
+                                    bf16* __restrict__ dS, int B, int lgH, int lgW, int lgG) {
+  const int H = 1 << lgH, W = 1 << lgW, C = 8 << lgG;
+  const long total = (long)B << (lgH + lgW + lgG);
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
-    const int c = (int)(i % cp) * 2;
-    long r = i / cp;
-    const int x = (int)(r % w2);
-    r /= w2;
-    const int y = (int)(r % h2), b = (int)(r / h2);
-    float2 s = make_float2(0.f, 0.f);
+    const OctIdx k = oct_idx(i, lgH, lgW, lgG);
+    Oct s = {};
     for (int q = 0; q < 4; ++q) {
-      const float2 v = ld_pair(dU, hidx(b, 2 * y + q / 2, 2 * x + q % 2, H, W, C) + c);
-      s.x += v.x;
-      s.y += v.y;
+      const Oct v = ld_oct(dU, hidx(k.b, 2 * k.y + q / 2, 2 * k.x + q % 2, 2 * H, 2 * W, C) + k.c);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) s.v[j] += v.v[j];
     }
-    const float2 m = ld_pair(Sact, hidx(b, y, x, h2, w2, C) + c);
-    st_pair(dS, b, y, x, h2, w2, C, c, m.x > 0.f ? s.x : 0.f, m.y > 0.f ? s.y : 0.f);
+    const Oct m = ld_oct(Sact, hidx(k.b, k.y, k.x, H, W, C) + k.c);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s.v[j] = m.v[j] > 0.f ? s.v[j] : 0.f;
+    st_oct(dS, k.b, k.y, k.x, H, W, C, k.c, s);
   }
 }
 
 // dS (H x W) = (skip + dP(pixel / 2) / 4) * (S > 0)
 __global__ void pool_grad_add_mask_kernel(const bf16* __restrict__ dP, const bf16* __restrict__ skip,
                                           const bf16* __restrict__ Sact, bf16* __restrict__ dS, int B,
-                                          int H, int W, int C) {
-  const int cp = C / 2;
-  const long total = (long)B * H * W * cp;
+                                          int lgH, int lgW, int lgG) {
+  const int H = 1 << lgH, W = 1 << lgW, C = 8 << lgG;
+  const long total = (long)B << (lgH + lgW + lgG);
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
-    const int c = (int)(i % cp) * 2;
-    long r = i / cp;
-    const int x = (int)(r % W);
-    r /= W;
-    const int y = (int)(r % H), b = (int)(r / H);
-    const float2 p = ld_pair(dP, hidx(b, y / 2, x / 2, H / 2, W / 2, C) + c);
-    const float2 k = ld_pair(skip, hidx(b, y, x, H, W, C) + c);
-    const float2 m = ld_pair(Sact, hidx(b, y, x, H, W, C) + c);
-    st_pair(dS, b, y, x, H, W, C, c, m.x > 0.f ? k.x + 0.25f * p.x : 0.f,
-            m.y > 0.f ? k.y + 0.25f * p.y : 0.f);
+    const OctIdx k = oct_idx(i, lgH, lgW, lgG);
+    const Oct p = ld_oct(dP, hidx(k.b, k.y / 2, k.x / 2, H / 2, W / 2, C) + k.c);
+    const Oct q = ld_oct(skip, hidx(k.b, k.y, k.x, H, W, C) + k.c);
+    const Oct m = ld_oct(Sact, hidx(k.b, k.y, k.x, H, W, C) + k.c);
+    Oct o;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) o.v[j] = m.v[j] > 0.f ? q.v[j] + 0.25f * p.v[j] : 0.f;
+    st_oct(dS, k.b, k.y, k.x, H, W, C, k.c, o);
   }
 }
 
-// mean of every (sample, layer) plane of h [B][n][H][W] into mean[B n]
-__global__ void plane_mean_kernel(const float* __restrict__ h, int HW, double* __restrict__ mean) {
-  const float* p = h + (long)blockIdx.x * HW;
-  double s = 0.0;
-  for (int i = threadIdx.x; i < HW; i += blockDim.x) s += p[i];
-  __shared__ double red[256];
-  red[threadIdx.x] = s;
+// ---------------------------------------------------------------------------
+// Per-plane sums of a [planes][HW] FP32 array in two levels, deterministic:
+// block (chunk, plane) adds kRedChunk elements (FP32 over a thread's 32
+// values, FP64 above that), and the last block to finish adds the chunk
+// sums of every plane in order.
+//   mode 0: out[p] = mean of plane p;
+//   mode 1: out[b] = RMS over the n planes of sample b of x - center[plane]
+//           (center: the plane means), zero for a flat sample.
+// counter: a zeroed word, left zeroed.
+// ---------------------------------------------------------------------------
+constexpr int kRedChunk = 8192;
+__global__ void __launch_bounds__(256) plane_reduce_kernel(const float* __restrict__ x, int planes,
+                                                           int HW, int n, int mode,
+                                                           const double* __restrict__ center,
+                                                           double* __restrict__ partial,
+                                                           unsigned* __restrict__ counter,
+                                                           double* __restrict__ out) {
+  const int nchunk = HW / kRedChunk, pl = blockIdx.y, ch = blockIdx.x;
+  const float4* p = reinterpret_cast<const float4*>(x + (long)pl * HW + (long)ch * kRedChunk);
+  const float c = mode ? (float)center[pl] : 0.f;
+  float s = 0.f;
+#pragma unroll
+  for (int k = 0; k < kRedChunk / 1024; ++k) {
+    const float4 v = p[k * 256 + threadIdx.x];
+    if (mode) {
+      const float d0 = v.x - c, d1 = v.y - c, d2 = v.z - c, d3 = v.w - c;
+      s += (d0 * d0 + d1 * d1) + (d2 * d2 + d3 * d3);
+    } else {
+      s += (v.x + v.y) + (v.z + v.w);
+    }
+  }
+  double d = s;
+  for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+  __shared__ double red[8];
+  __shared__ bool last;
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = d;
   __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    partial[(long)pl * nchunk + ch] = t;
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x * gridDim.y - 1;
   }
-  if (threadIdx.x == 0) mean[blockIdx.x] = red[0] / HW;
-}
-
-// RMS over all layers and pixels of sample b of h - mean (one block per
-// sample), into rms[b]; zero for a flat sample
-__global__ void sample_rms_kernel(const float* __restrict__ h, const double* __restrict__ mean,
-                                  int n, int HW, double* __restrict__ rms) {
-  const float* p = h + (long)blockIdx.x * n * HW;
-  double s = 0.0;
-  for (long i = threadIdx.x; i < (long)n * HW; i += blockDim.x) {
-    const double d = (double)p[i] - mean[blockIdx.x * n + i / HW];
-    s += d * d;
-  }
-  __shared__ double red[256];
-  red[threadIdx.x] = s;
   __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (mode == 0) {
+    for (int q = threadIdx.x; q < planes; q += blockDim.x) {
+      double t = 0.0;
+      for (int k = 0; k < nchunk; ++k) t += __ldcg(partial + (long)q * nchunk + k);
+      out[q] = t / HW;
+    }
+  } else {
+    for (int b = threadIdx.x; b < planes / n; b += blockDim.x) {
+      double t = 0.0;
+      for (int q = b * n; q < b * n + n; ++q)
+        for (int k = 0; k < nchunk; ++k) t += __ldcg(partial + (long)q * nchunk + k);
+      out[b] = sqrt(t / ((double)n * HW));
+    }
   }
-  if (threadIdx.x == 0) rms[blockIdx.x] = sqrt(red[0] / ((double)n * HW));
+  if (threadIdx.x == 0) *counter = 0u;
 }
 
 // 1 / s of a sample, 0 for a flat one (its planes are then all zero)
@@ -628,20 +699,33 @@ __global__ void loss_kernel(const float* __restrict__ y, const float* __restrict
   if (threadIdx.x == 0) atomicAdd(loss, red[0]);
 }
 
-// db[c] += sum over the real pixels of dz (NHWC halo, C channels)
-__global__ void bias_grad_kernel(const bf16* __restrict__ dz, int B, int H, int W, int C,
-                                 float* __restrict__ db) {
-  const int c = threadIdx.x;  // blockDim.x = C
-  const long total = (long)B * H * W;
-  const long per = (total + gridDim.x - 1) / gridDim.x;
-  const long p0 = blockIdx.x * per, p1 = p0 + per < total ? p0 + per : total;
-  float s = 0.f;
-  for (long p = p0; p < p1; ++p) {
-    const int x = (int)(p % W);
-    const int y = (int)((p / W) % H), b = (int)(p / ((long)W * H));
-    s += __bfloat162float(dz[hidx(b, y, x, H, W, C) + c]);
+// db[c] += sum over the real pixels of dz (NHWC halo, C channels, C = 8 2^lgG
+// <= 256). A thread adds one 8-channel group over every (256 / groups)-th
+// pixel of the grid-stride loop; the block combines its threads' sums in
+// shared memory and adds one atomic per channel.
+__global__ void __launch_bounds__(256) bias_grad_kernel(const bf16* __restrict__ dz, int B, int lgH,
+                                                        int lgW, int lgG, float* __restrict__ db) {
+  const int H = 1 << lgH, W = 1 << lgW, C = 8 << lgG, g = 1 << lgG;
+  const int pp = 256 >> lgG;  // pixels per block and iteration
+  const int grp = threadIdx.x & (g - 1), sub = threadIdx.x >> lgG;
+  const long npix = (long)B << (lgH + lgW);
+  float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (long q = (long)blockIdx.x * pp + sub; q < npix; q += (long)gridDim.x * pp) {
+    const int x = (int)(q & (W - 1)), y = (int)((q >> lgW) & (H - 1)), b = (int)(q >> (lgW + lgH));
+    const Oct v = ld_oct(dz, hidx(b, y, x, H, W, C) + grp * 8);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s[j] += v.v[j];
   }
-  if (c < C) atomicAdd(db + c, s);
+  __shared__ float red[256][9];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) red[threadIdx.x][j] = s[j];
+  __syncthreads();
+  if ((int)threadIdx.x < C) {
+    const int gi = threadIdx.x >> 3, j = threadIdx.x & 7;
+    float t = 0.f;
+    for (int k = 0; k < pp; ++k) t += red[k * g + gi][j];
+    atomicAdd(db + threadIdx.x, t);
+  }
 }
 
 struct LayerParams {
@@ -825,6 +909,12 @@ int grid_for(long work, int threads) {
   return (int)std::max(1L, std::min(g, 4096L));
 }
 
+int ilog2(int v) {
+  int k = 0;
+  while ((1 << (k + 1)) <= v) ++k;
+  return k;
+}
+
 }  // namespace
 
 struct mlswlbm_unet {
@@ -839,6 +929,8 @@ struct mlswlbm_unet {
   float* hbuf;                            // predicted heights scratch (train: unused)
   double* means;                          // per (sample, layer) means
   double* rms;                            // per sample RMS deviation
+  double* red_part;                       // chunk sums of plane_reduce_kernel
+  unsigned* red_count;                    // its completion counter (zero between launches)
   double* dloss;
   float* extra;                           // parameter planes' values
   float *params, *pgrad, *adam_m, *adam_v;
@@ -866,6 +958,8 @@ void unet_free(mlswlbm_unet* u) {
   cudaFree(u->hbuf);
   cudaFree(u->means);
   cudaFree(u->rms);
+  cudaFree(u->red_part);
+  cudaFree(u->red_count);
   cudaFree(u->dloss);
   cudaFree(u->extra);
   cudaFree(u->params);
@@ -988,16 +1082,26 @@ cudaError_t weight_grad(mlswlbm_unet* u, int l, int batch) {
                                           : launch_wgrad_t<256>(a, grid, u->stream));
     if (e != cudaSuccess) return e;
   }
-  const int tz_c = N.cout;
-  bias_grad_kernel<<<std::max(1, std::min(2048, batch * H * W / 256)), tz_c, 0, u->stream>>>(
-      u->grad[tz], batch, H, W, tz_c, u->pgrad + u->L[l].b_off);
+  // the output gradient has the layer's cout channels (YG: kCout)
+  const int Cz = kTC[tz];
+  const int bgrid = (int)std::max(1L, std::min((long)4 * u->num_sms, (long)batch * H * W * (Cz / 8) / 256));
+  bias_grad_kernel<<<bgrid, 256, 0, u->stream>>>(u->grad[tz], batch, ilog2(H), ilog2(W),
+                                                 ilog2(Cz / 8), u->pgrad + u->L[l].b_off);
   return cudaGetLastError();
+}
+
+// plane means (mode 0) or sample RMS deviations about u->means (mode 1) of
+// a [batch][n][H][W] FP32 array
+void plane_reduce(mlswlbm_unet* u, const float* x, int batch, int mode, double* out) {
+  const int HW = u->H * u->W;
+  plane_reduce_kernel<<<dim3(HW / kRedChunk, batch * u->n), 256, 0, u->stream>>>(
+      x, batch * u->n, HW, u->n, mode, u->means, u->red_part, u->red_count, out);
 }
 
 cudaError_t forward(mlswlbm_unet* u, const float* h, int batch) {
   const int HW = u->H * u->W;
-  plane_mean_kernel<<<batch * u->n, 256, 0, u->stream>>>(h, HW, u->means);
-  sample_rms_kernel<<<batch, 256, 0, u->stream>>>(h, u->means, u->n, HW, u->rms);
+  plane_reduce(u, h, batch, 0, u->means);
+  plane_reduce(u, h, batch, 1, u->rms);
   input_kernel<<<grid_for((long)batch * HW, 256), 256, 0, u->stream>>>(
       h, u->means, u->rms, batch, u->n, u->H, u->W, u->in_scale, u->extra, u->n_extra, u->act[X0]);
   cudaError_t e = cudaGetLastError();
@@ -1011,12 +1115,13 @@ cudaError_t forward(mlswlbm_unet* u, const float* h, int batch) {
     for (const Pre& p : pre) {
       if (p.layer != l) continue;
       const int C = kTC[p.dst], Hd = u->lh[p.dst], Wd = u->lw[p.dst];
+      const int grid = grid_for((long)batch * Hd * Wd * C / 8, 256);
       if (p.up)
-        up_kernel<<<grid_for((long)batch * Hd * Wd * C / 2, 256), 256, 0, u->stream>>>(
-            u->act[p.src], u->act[p.dst], batch, Hd, Wd, C);
+        up_kernel<<<grid, 256, 0, u->stream>>>(u->act[p.src], u->act[p.dst], batch, ilog2(Hd),
+                                               ilog2(Wd), ilog2(C / 8));
       else
-        pool_kernel<<<grid_for((long)batch * Hd * Wd * C / 2, 256), 256, 0, u->stream>>>(
-            u->act[p.src], u->act[p.dst], batch, u->lh[p.src], u->lw[p.src], C);
+        pool_kernel<<<grid, 256, 0, u->stream>>>(u->act[p.src], u->act[p.dst], batch, ilog2(Hd),
+                                                 ilog2(Wd), ilog2(C / 8));
       e = cudaGetLastError();
       if (e != cudaSuccess) return e;
     }
@@ -1037,14 +1142,14 @@ cudaError_t backward(mlswlbm_unet* u, int batch) {
   auto Aq = [&](int t) { return (const bf16*)u->act[t]; };
   auto upmask = [&](int dU, int S, int dS) {
     const int C = kTC[S], H = u->lh[dU], W = u->lw[dU];
-    up_grad_mask_kernel<<<grid_for((long)batch * (H / 2) * (W / 2) * C / 2, 256), 256, 0, u->stream>>>(
-        G(dU), Aq(S), G(dS), batch, H, W, C);
+    up_grad_mask_kernel<<<grid_for((long)batch * (H / 2) * (W / 2) * C / 8, 256), 256, 0, u->stream>>>(
+        G(dU), Aq(S), G(dS), batch, ilog2(H / 2), ilog2(W / 2), ilog2(C / 8));
     return cudaGetLastError();
   };
   auto poolmask = [&](int dP, int lev, int S) {
     const int C = kTC[S], H = u->lh[S], W = u->lw[S];
-    pool_grad_add_mask_kernel<<<grid_for((long)batch * H * W * C / 2, 256), 256, 0, u->stream>>>(
-        G(dP), u->skipg[lev], Aq(S), G(S), batch, H, W, C);
+    pool_grad_add_mask_kernel<<<grid_for((long)batch * H * W * C / 8, 256), 256, 0, u->stream>>>(
+        G(dP), u->skipg[lev], Aq(S), G(S), batch, ilog2(H), ilog2(W), ilog2(C / 8));
     return cudaGetLastError();
   };
   // layer 14 (out) .. 0, see the table
@@ -1129,7 +1234,8 @@ int mlswlbm_unet_create(int n_layers, int nx, int ny, int max_batch, int n_extra
       !std::isfinite(in_scale) || !std::isfinite(out_scale))
     return MLSW_ERR_ARG;
   // four levels, the coarsest at least 16 x 16 cells
-  if (!is_pow2(nx) || !is_pow2(ny) || nx < 128 || ny < 128 || nx > 4096 || ny > 4096)
+  if (!is_pow2(nx) || !is_pow2(ny) || nx < 128 || ny < 128 || nx > 4096 || ny > 4096 ||
+      (long)max_batch * n_layers > 65535)
     return MLSW_ERR_UNSUPPORTED;
   for (int j = 0; j < n_extra; ++j)
     if (!std::isfinite(extra[j])) return MLSW_ERR_ARG;
@@ -1186,6 +1292,10 @@ int mlswlbm_unet_create(int n_layers, int nx, int ny, int max_batch, int n_extra
        cudaMalloc(&u->hbuf, hsz * sizeof(float)) == cudaSuccess &&
        cudaMalloc(&u->means, (size_t)max_batch * n_layers * sizeof(double)) == cudaSuccess &&
        cudaMalloc(&u->rms, (size_t)max_batch * sizeof(double)) == cudaSuccess &&
+       cudaMalloc(&u->red_part, (size_t)max_batch * n_layers * (nx * ny / kRedChunk) *
+                                    sizeof(double)) == cudaSuccess &&
+       cudaMalloc(&u->red_count, sizeof(unsigned)) == cudaSuccess &&
+       cudaMemsetAsync(u->red_count, 0, sizeof(unsigned), u->stream) == cudaSuccess &&
        cudaMalloc(&u->dloss, sizeof(double)) == cudaSuccess &&
        cudaMalloc(&u->extra, (size_t)kCin0 * sizeof(float)) == cudaSuccess &&
        cudaMalloc(&u->params, u->nparam * sizeof(float)) == cudaSuccess &&
@@ -1256,7 +1366,7 @@ int mlswlbm_unet_predict(mlswlbm_unet* u, const float* h, float* out, int batch)
   if (!u || !h || !out || batch < 1 || batch > u->Bmax || out == h) return MLSW_ERR_ARG;
   if (forward(u, h, batch) != cudaSuccess) return MLSW_ERR_CUDA;
   const int HW = u->H * u->W;
-  plane_mean_kernel<<<batch * u->n, 256, 0, u->stream>>>(u->ydense, HW, u->means);
+  plane_reduce(u, u->ydense, batch, 0, u->means);
   const long total = (long)batch * u->n * HW;
   output_kernel<<<grid_for(total, 256), 256, 0, u->stream>>>(h, u->ydense, u->means, u->rms, total,
                                                               u->n, HW, 1.f / u->out_scale, out);
