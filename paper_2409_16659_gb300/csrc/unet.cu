@@ -109,20 +109,34 @@ struct ConvArgs {
   int* err;
 };
 
+// A convolution tile is 128 output pixels, 16 wide and 8 high. For every
+// input, chunk of KC channels and column shift sx in {-1, 0, 1}, one TMA copy
+// brings the 16 x 10 pixels of that shift (rows y0 - 1 .. y0 + 8): a K-major
+// operand of 160 rows whose rows 16 (sy + 1) .. + 127 are the tile's pixels
+// shifted by (sx, sy). The three row shifts share the copy (an offset of 16
+// rows is a whole number of swizzle atoms) and each takes the weights of
+// its own tap, one copy of BN x KC. Two rings of stages: shifted pixels (A)
+// and weights (B).
 template <int KC, int BN>
 struct ConvShape {
-  static constexpr int ABYTES = 128 * KC * 2, BBYTES = BN * KC * 2;
+  static constexpr int TW = 16, TH = 8;        // the tile of output pixels
+  static constexpr int AROWS = TW * (TH + 2);  // rows of a shifted box
+  static constexpr int ABYTES = AROWS * KC * 2, BBYTES = BN * KC * 2;
   static constexpr int ASTRIDE = (ABYTES + 1023) / 1024 * 1024;
   static constexpr int BSTRIDE = (BBYTES + 1023) / 1024 * 1024;
-  static constexpr int STAGE = ASTRIDE + BSTRIDE;
-  static constexpr int ST = (150 * 1024 / STAGE) > 8 ? 8 : (150 * 1024 / STAGE);
+  static constexpr int STA = 4;
+  static constexpr int STB0 = (200 * 1024 - STA * ASTRIDE) / BSTRIDE;
+  static constexpr int STB = STB0 > 12 ? 12 : (STB0 < 2 ? 2 : STB0);
   static constexpr int ACOLS = BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
   static constexpr int TCOLS = 2 * ACOLS;          // two accumulators
   static constexpr int CTAS_TMEM = 512 / TCOLS;    // CTAs whose TMEM fits one SM
-  static constexpr size_t SMEM_NEED = 1024 + (size_t)ST * STAGE + 256;
+  static constexpr size_t SMEM_NEED =
+      1024 + (size_t)STA * ASTRIDE + (size_t)STB * BSTRIDE + 8 * (2 * STA + 2 * STB + 5) + 16;
   // ask for enough shared memory that no more CTAs than CTAS_TMEM share an SM
   static constexpr size_t SMEM_TMEM = 233472 / (CTAS_TMEM + 1) + 1024;
   static constexpr size_t SMEM = SMEM_NEED > SMEM_TMEM ? SMEM_NEED : SMEM_TMEM;
+  static_assert(SMEM_NEED <= 232448, "stages exceed shared memory");
+  static_assert((16 * KC * 2) % (8 * KC * 2) == 0, "row shifts are whole swizzle atoms");
 };
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
@@ -130,36 +144,40 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   return *reinterpret_cast<uint32_t*>(&h);
 }
 
-// Persistent and warp-specialised: warp 0 issues the TMA copies of every
-// (tile, tap, channel chunk) stage, warp 1 the MMAs into one of two TMEM
-// accumulators, warps 2..5 drain a finished accumulator (epilogue) while
-// the next tile accumulates into the other. Work item w of the CTA is tile
-// w / ntn, output-channel tile w % ntn, for w = blockIdx.x, + gridDim.x, ...
+// Persistent and warp-specialised: warp 0 issues the TMA copies, warp 1
+// the MMAs into one of two TMEM accumulators, warps 2..5 drain a finished
+// accumulator (epilogue) while the next tile accumulates into the other.
+// Work item w of the CTA is tile w / ntn, output-channel tile w % ntn, for
+// w = blockIdx.x, + gridDim.x, ...
 template <int KC, int BN>
 __global__ void __launch_bounds__(192) conv_tc(const __grid_constant__ ConvArgs a, int ntn) {
   using S = ConvShape<KC, BN>;
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
   unsigned char* sA = sm;
-  unsigned char* sB = sm + S::ST * S::ASTRIDE;
-  uint64_t* full = (uint64_t*)(sB + S::ST * S::BSTRIDE);
-  uint64_t* empty = full + S::ST;
-  uint64_t* tfull = empty + S::ST;   // [2] accumulator ready
-  uint64_t* tempty = tfull + 2;      // [2] accumulator drained
-  uint64_t* drain = tempty + 2;      // every MMA of this CTA has completed
+  unsigned char* sB = sm + S::STA * S::ASTRIDE;
+  uint64_t* fullA = (uint64_t*)(sB + S::STB * S::BSTRIDE);
+  uint64_t* emptyA = fullA + S::STA;
+  uint64_t* fullB = emptyA + S::STA;
+  uint64_t* emptyB = fullB + S::STB;
+  uint64_t* tfull = emptyB + S::STB;  // [2] accumulator ready
+  uint64_t* tempty = tfull + 2;       // [2] accumulator drained
+  uint64_t* drain = tempty + 2;       // every MMA of this CTA has completed
   uint32_t* tslot = (uint32_t*)(drain + 1);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int W = a.W, H = a.H;
-  const int BX = W < 128 ? W : 128, BY = 128 / BX;
-  const int tpr = W / BX, tpi = tpr * (H / BY);
+  const int tpr = W / S::TW, tpi = tpr * (H / S::TH);
   const int nitems = a.B_tiles * ntn;
-  int nk = 0;
-  for (int i = 0; i < a.nin; ++i) nk += 9 * (a.cin[i] / KC);
+  const int sgn = a.reverse_taps ? -1 : 1;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < S::ST; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+    for (int s = 0; s < S::STA; ++s) {
+      mbar_init(&fullA[s], 1);
+      mbar_init(&emptyA[s], 1);
+    }
+    for (int s = 0; s < S::STB; ++s) {
+      mbar_init(&fullB[s], 1);
+      mbar_init(&emptyB[s], 1);
     }
     for (int j = 0; j < 2; ++j) {
       mbar_init(&tfull[j], 1);
@@ -176,49 +194,68 @@ __global__ void __launch_bounds__(192) conv_tc(const __grid_constant__ ConvArgs 
   bool ok = true;
   if (warp == 0) {
     if (lane == 0) {
-      int kb = 0;  // stage counter over all items
+      int ka = 0, kb = 0;  // stage counters over all items
       for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
         const int tile = item / ntn, n0 = (item % ntn) * BN;
         const int b = tile / tpi, r = tile % tpi;
-        const int x0 = (r % tpr) * BX, y0 = (r / tpr) * BY;
+        const int x0 = (r % tpr) * S::TW, y0 = (r / tpr) * S::TH;
         for (int i = 0; i < a.nin && ok; ++i)
-          for (int tap = 0; tap < 9 && ok; ++tap)
-            for (int c0 = 0; c0 < a.cin[i] && ok; c0 += KC, ++kb) {
-              const int s = kb % S::ST, it = kb / S::ST;
-              if (it > 0) ok = mbar_wait_bounded(&empty[s], (it - 1) & 1);
+          for (int c0 = 0; c0 < a.cin[i] && ok; c0 += KC)
+            for (int sx = -1; sx <= 1 && ok; ++sx, ++ka) {
+              const int sa = ka % S::STA, ita = ka / S::STA;
+              if (ita > 0) ok = mbar_wait_bounded(&emptyA[sa], (ita - 1) & 1);
               if (!ok) break;
-              mbar_arrive_expect_tx(&full[s], (uint32_t)(S::ABYTES + S::BBYTES));
-              int dx = tap % 3 - 1, dy = tap / 3 - 1;
-              if (a.reverse_taps) {
-                dx = -dx;
-                dy = -dy;
+              mbar_arrive_expect_tx(&fullA[sa], (uint32_t)S::ABYTES);
+              // halo coordinates: real column x0 + sx is x0 + sx + 1, real
+              // row y0 - 1 is y0
+              tma_load_4d(sA + sa * S::ASTRIDE, &a.in_map[i], &fullA[sa], c0, x0 + sx + 1, y0, b);
+              for (int sy = -1; sy <= 1 && ok; ++sy, ++kb) {
+                const int sb = kb % S::STB, itb = kb / S::STB;
+                if (itb > 0) ok = mbar_wait_bounded(&emptyB[sb], (itb - 1) & 1);
+                if (!ok) break;
+                // the tap whose pixel is at shift (sx, sy)
+                const int tap = 3 * (sgn * sy + 1) + (sgn * sx + 1);
+                mbar_arrive_expect_tx(&fullB[sb], (uint32_t)S::BBYTES);
+                tma_load_2d(sB + sb * S::BSTRIDE, &a.w_map, &fullB[sb],
+                            tap * a.cin_tot + a.koff[i] + c0, n0);
               }
-              tma_load_4d(sA + s * S::ASTRIDE, &a.in_map[i], &full[s], c0, x0 + dx + 1, y0 + dy + 1, b);
-              tma_load_2d(sB + s * S::BSTRIDE, &a.w_map, &full[s], tap * a.cin_tot + a.koff[i] + c0, n0);
             }
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_bf16_f32(128, BN);
-      int kb = 0, local = 0;
+      int ka = 0, kb = 0, local = 0;
       for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x, ++local) {
         const int ab = local & 1, use = local >> 1;
         if (use > 0) ok = mbar_wait_bounded(&tempty[ab], (use - 1) & 1);
         if (!ok) break;
         tc_fence_after();
         const uint32_t acc = tmem + (uint32_t)(ab * S::ACOLS);
-        for (int k = 0; k < nk && ok; ++k, ++kb) {
-          const int s = kb % S::ST, it = kb / S::ST;
-          ok = mbar_wait_bounded(&full[s], it & 1);
-          if (!ok) break;
-          tc_fence_after();
+        uint32_t accumulate = 0;
+        for (int i = 0; i < a.nin && ok; ++i)
+          for (int c0 = 0; c0 < a.cin[i] && ok; c0 += KC)
+            for (int sx = 0; sx < 3 && ok; ++sx, ++ka) {
+              const int sa = ka % S::STA, ita = ka / S::STA;
+              ok = mbar_wait_bounded(&fullA[sa], ita & 1);
+              if (!ok) break;
+              for (int sy = 0; sy < 3 && ok; ++sy, ++kb) {
+                const int sb = kb % S::STB, itb = kb / S::STB;
+                ok = mbar_wait_bounded(&fullB[sb], itb & 1);
+                if (!ok) break;
+                tc_fence_after();
+                const unsigned char* pa = sA + sa * S::ASTRIDE + sy * S::TW * KC * 2;
+                const unsigned char* pb = sB + sb * S::BSTRIDE;
 #pragma unroll
-          for (int kk = 0; kk < KC / 16; ++kk)
-            tc_mma(acc, sdesc_kmajor<KC * 2>(sA + s * S::ASTRIDE + kk * 32),
-                   sdesc_kmajor<KC * 2>(sB + s * S::BSTRIDE + kk * 32), idesc, (k | kk) ? 1u : 0u);
-          tc_commit(&empty[s]);
-        }
+                for (int kk = 0; kk < KC / 16; ++kk) {
+                  tc_mma(acc, sdesc_kmajor<KC * 2>(pa + kk * 32), sdesc_kmajor<KC * 2>(pb + kk * 32),
+                         idesc, accumulate);
+                  accumulate = 1;
+                }
+                tc_commit(&emptyB[sb]);
+              }
+              tc_commit(&emptyA[sa]);
+            }
         tc_commit(&tfull[ab]);
       }
       // no MMA may still run when the tensor memory is freed
@@ -239,9 +276,9 @@ __global__ void __launch_bounds__(192) conv_tc(const __grid_constant__ ConvArgs 
       }
       const int tile = item / ntn, n0 = (item % ntn) * BN;
       const int b = tile / tpi, r = tile % tpi;
-      const int x0 = (r % tpr) * BX, y0 = (r / tpr) * BY;
+      const int x0 = (r % tpr) * S::TW, y0 = (r / tpr) * S::TH;
       const int m = q * 32 + lane;
-      const int x = x0 + m % BX, y = y0 + m / BX;
+      const int x = x0 + (m & (S::TW - 1)), y = y0 + m / S::TW;
       const int xs[2] = {x + 1, x == 0 ? W + 1 : (x == W - 1 ? 0 : -1)};
       const int ys[2] = {y + 1, y == 0 ? H + 1 : (y == H - 1 ? 0 : -1)};
 #pragma unroll 1
@@ -309,29 +346,37 @@ __global__ void __launch_bounds__(192) conv_tc(const __grid_constant__ ConvArgs 
 // ---------------------------------------------------------------------------
 // Weight gradient of one input of a layer on tcgen05:
 //   dW[o][t][koff + c] += sum_p dz[p][o] x[p + off(t)][c]
-// a GEMM over pixels p (K) of two MN-major operands: the output gradient
-// (M = output channels, tiles of 128) and the shifted input (N = input
-// channels, tiles of BN). A pixel chunk is 64 pixels (a box of
-// min(W, 64) x 64 / min(W, 64)); channels beyond a tensor's read as zero.
+// a GEMM over pixels p (K) of two MN-major operands (channels contiguous):
+// the output gradient (M = output channels, tiles of 128) and the input
+// (N = input channels, tiles of BN). A CTA takes one column shift dx of the
+// taps and a run of 8 x 8-pixel chunks. Per chunk one copy brings the
+// output gradient (64 K rows) and one the input's 8 x 10 pixels of the
+// chunk's columns shifted by dx (rows y0 - 1 .. y0 + 8, 80 K rows); the
+// three taps of the column (dy = -1, 0, 1) read the latter at K offsets of
+// 0, 8 and 16 rows (whole swizzle atoms) into three TMEM accumulators.
+// Channels beyond a tensor's read as zero; the CTAs' sums are added with
+// FP32 atomics.
 // ---------------------------------------------------------------------------
 struct WgradArgs {
-  CUtensorMap dz_map;  // 4-D [Cout, W+2, H+2, B], box [64, BXK, BYK, 1]
-  CUtensorMap x_map;   // 4-D [Cin, W+2, H+2, B], box [64, BXK, BYK, 1]
+  CUtensorMap dz_map;  // 4-D [Cout, W+2, H+2, B], box [64, 8, 8, 1]
+  CUtensorMap x_map;   // 4-D [Cin, W+2, H+2, B], box [64, 8, 10, 1]
   int H, W, B;
   int cout, cin, koff, cin_tot;
-  int chunks_per_cta;  // pixel chunks of 64 per CTA
+  int chunks_per_cta;  // 8 x 8-pixel chunks per CTA
   float* dw;           // [cout][9][cin_tot]
   int* err;
 };
 
 template <int BN>
 struct WgShape {
-  static constexpr int BOX = 64 * 128;  // 64 pixels x 64 channels of BF16
-  static constexpr int ABYTES = 2 * BOX, BBYTES = (BN / 64) * BOX;
+  static constexpr int ABOX = 64 * 128;  // 64 K rows x 64 channels of BF16
+  static constexpr int BBOX = 80 * 128;  // 80 K rows x 64 channels
+  static constexpr int ABYTES = 2 * ABOX, BBYTES = (BN / 64) * BBOX;
   static constexpr int STAGE = ABYTES + BBYTES;
   static constexpr int ST = (190 * 1024 / STAGE) > 6 ? 6 : (190 * 1024 / STAGE);
-  static constexpr int TCOLS = BN <= 64 ? 64 : (BN <= 128 ? 128 : 256);
+  static constexpr int TCOLS = 3 * BN <= 256 ? 256 : 512;  // three accumulators of BN columns
   static constexpr size_t SMEM = 1024 + (size_t)ST * STAGE + 256;
+  static_assert(3 * BN <= 512, "three accumulators must fit the tensor memory");
 };
 
 template <int BN>
@@ -344,16 +389,17 @@ __global__ void __launch_bounds__(128) wgrad_tc(const __grid_constant__ WgradArg
   uint64_t* done = empty + S::ST;
   uint32_t* tslot = (uint32_t*)(done + 1);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int tap = blockIdx.y % 9, mt = blockIdx.y / 9, nt = blockIdx.z;
+  const int dx = blockIdx.y % 3 - 1, mt = blockIdx.y / 3, nt = blockIdx.z;
   const int m0 = mt * 128, c0 = nt * BN;
   const int W = a.W, H = a.H;
-  const int BXK = W < 64 ? W : 64, BYK = 64 / BXK;
-  const int cpr = W / BXK, cpi = cpr * (H / BYK);  // chunks per row of chunks, per image
+  const int cpr = W / 8, cpi = cpr * (H / 8);  // chunks per row of chunks, per image
   const long total = (long)a.B * cpi;
   const long k_first = (long)blockIdx.x * a.chunks_per_cta;
   const long k_end = k_first + a.chunks_per_cta < total ? k_first + a.chunks_per_cta : total;
   const int nk = k_end > k_first ? (int)(k_end - k_first) : 0;
-  const int dx = tap % 3 - 1, dy = tap / 3 - 1;
+  // output-gradient boxes holding real channels (the rest of the A tile
+  // feeds accumulator rows that are never read)
+  const int na = a.cout > m0 + 64 ? 2 : 1;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S::ST; ++s) {
@@ -376,14 +422,16 @@ __global__ void __launch_bounds__(128) wgrad_tc(const __grid_constant__ WgradArg
       if (!ok) break;
       const long k = k_first + kb;
       const int b = (int)(k / cpi), q = (int)(k % cpi);
-      const int px = (q % cpr) * BXK, py = (q / cpr) * BYK;
+      const int px = (q % cpr) * 8, py = (q / cpr) * 8;
       unsigned char* st = sm + s * S::STAGE;
-      mbar_arrive_expect_tx(&full[s], (uint32_t)S::STAGE);
-      for (int j = 0; j < 2; ++j)
-        tma_load_4d(st + j * S::BOX, &a.dz_map, &full[s], m0 + 64 * j, px + 1, py + 1, b);
+      mbar_arrive_expect_tx(&full[s], (uint32_t)(na * S::ABOX + S::BBYTES));
+      for (int j = 0; j < na; ++j)
+        tma_load_4d(st + j * S::ABOX, &a.dz_map, &full[s], m0 + 64 * j, px + 1, py + 1, b);
+      // halo coordinates: real column px + dx is px + dx + 1, real row
+      // py - 1 is py
       for (int j = 0; j < BN / 64; ++j)
-        tma_load_4d(st + S::ABYTES + j * S::BOX, &a.x_map, &full[s], c0 + 64 * j, px + dx + 1,
-                    py + dy + 1, b);
+        tma_load_4d(st + S::ABYTES + j * S::BBOX, &a.x_map, &full[s], c0 + 64 * j, px + dx + 1,
+                    py, b);
     }
   } else if (warp == 1 && lane == 0) {
     constexpr uint32_t idesc = idesc_bf16_f32(128, BN, true, true);
@@ -394,10 +442,12 @@ __global__ void __launch_bounds__(128) wgrad_tc(const __grid_constant__ WgradArg
       tc_fence_after();
       unsigned char* st = sm + s * S::STAGE;
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk)
-        tc_mma(tmem, sdesc_mnmajor128(st + kk * 16 * 128, S::BOX),
-               sdesc_mnmajor128(st + S::ABYTES + kk * 16 * 128, S::BOX), idesc,
-               (kb | kk) ? 1u : 0u);
+      for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+          tc_mma(tmem + (uint32_t)(j * BN), sdesc_mnmajor128(st + kk * 16 * 128, S::ABOX),
+                 sdesc_mnmajor128(st + S::ABYTES + (j * 8 + kk * 16) * 128, S::BBOX), idesc,
+                 (kb | kk) ? 1u : 0u);
       tc_commit(&empty[s]);
     }
     tc_commit(done);
@@ -408,14 +458,18 @@ __global__ void __launch_bounds__(128) wgrad_tc(const __grid_constant__ WgradArg
   if (dok && nk > 0) {
     const int o = m0 + warp * 32 + lane;
 #pragma unroll 1
-    for (int c = 0; c < BN; c += 16) {
-      uint32_t rr[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, rr);
-      if (o >= a.cout) continue;
-      for (int j = 0; j < 16; ++j) {
-        const int ci = c0 + c + j;
-        if (ci < a.cin)
-          atomicAdd(a.dw + ((long)o * 9 + tap) * a.cin_tot + a.koff + ci, __uint_as_float(rr[j]));
+    for (int j = 0; j < 3; ++j) {
+      const int tap = 3 * j + dx + 1;
+#pragma unroll 1
+      for (int c = 0; c < BN; c += 16) {
+        uint32_t rr[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(j * BN + c), rr);
+        if (o >= a.cout) continue;
+        for (int i = 0; i < 16; ++i) {
+          const int ci = c0 + c + i;
+          if (ci < a.cin)
+            atomicAdd(a.dw + ((long)o * 9 + tap) * a.cin_tot + a.koff + ci, __uint_as_float(rr[i]));
+        }
       }
     }
   } else if (!dok && threadIdx.x == 0) {
@@ -847,7 +901,7 @@ int bn_bwd(int l) {
   if (kNet[l].in[1] >= 0) bn = std::min(bn, kTC[kNet[l].in[1]]);
   return std::min(bn, 256);
 }
-int bn_wgrad(int cin) { return cin <= 64 ? 64 : (cin <= 128 ? 128 : 256); }
+int bn_wgrad(int cin) { return cin <= 64 ? 64 : 128; }
 
 template <int KC, int BN>
 cudaError_t launch_conv_t(const ConvArgs& a, int ntn, int num_sms, cudaStream_t st) {
@@ -1010,8 +1064,7 @@ cudaError_t conv_forward(mlswlbm_unet* u, int l, int batch) {
     a.dense_c = u->n;
   }
   a.err = u->err;
-  const int BX = std::min(a.W, 128), BY = 128 / BX;
-  a.B_tiles = batch * (a.W / BX) * (a.H / BY);
+  a.B_tiles = batch * (a.W / 16) * (a.H / 8);
   return launch_conv(kc_fwd(l), N.cout, a, 1, u->num_sms, u->stream);
 }
 
@@ -1043,8 +1096,7 @@ cudaError_t conv_input_grad(mlswlbm_unet* u, int l, int batch, bf16* out0, const
     a.out_c[1] = kTC[N.in[1]];
   }
   a.err = u->err;
-  const int BX = std::min(a.W, 128), BY = 128 / BX;
-  a.B_tiles = batch * (a.W / BX) * (a.H / BY);
+  a.B_tiles = batch * (a.W / 16) * (a.H / 8);
   const int bn = bn_bwd(l);
   return launch_conv(kc_bwd(l), bn, a, a.cout / bn, u->num_sms, u->stream);
 }
@@ -1072,14 +1124,13 @@ cudaError_t weight_grad(mlswlbm_unet* u, int l, int batch) {
     const int bn = bn_wgrad(a.cin);
     const int mt = (a.cout + 127) / 128, nt = (a.cin + bn - 1) / bn;
     const long chunks = (long)batch * H * W / 64;
-    // about four CTAs per SM over all taps and tiles
-    const long want = std::max(1L, (long)4 * u->num_sms / (9L * mt * nt));
+    // about two CTAs per SM over the three column shifts and all tiles
+    const long want = std::max(1L, (long)2 * u->num_sms / (3L * mt * nt));
     const int per = (int)std::max(1L, (chunks + want - 1) / want);
-    const dim3 grid((unsigned)((chunks + per - 1) / per), (unsigned)(9 * mt), (unsigned)nt);
+    const dim3 grid((unsigned)((chunks + per - 1) / per), (unsigned)(3 * mt), (unsigned)nt);
     a.chunks_per_cta = per;
     cudaError_t e = bn == 64 ? launch_wgrad_t<64>(a, grid, u->stream)
-                             : (bn == 128 ? launch_wgrad_t<128>(a, grid, u->stream)
-                                          : launch_wgrad_t<256>(a, grid, u->stream));
+                             : launch_wgrad_t<128>(a, grid, u->stream);
     if (e != cudaSuccess) return e;
   }
   // the output gradient has the layer's cout channels (YG: kCout)
@@ -1323,15 +1374,14 @@ int mlswlbm_unet_create(int n_layers, int nx, int ny, int max_batch, int n_extra
   }
   for (int t = 0; t < kTensors && ok; ++t) {
     const int W = u->lw[t], H = u->lh[t], C = kTC[t];
-    const int bx = std::min(W, 128), by = 128 / bx;
-    const int bxk = std::min(W, 64), byk = 64 / bxk;
     const int kc = act_kc(t);
-    if (kc) ok = map_nhwc(&u->act_map[t], u->act[t], C, W, H, max_batch, kc, bx, by);
+    // convolution inputs: boxes of 16 x 10 pixels (a tile and its row halo)
+    if (kc) ok = map_nhwc(&u->act_map[t], u->act[t], C, W, H, max_batch, kc, 16, 10);
     // the gradient of a convolution's output feeds its input-gradient
     // convolution with channel chunks of min(64, C)
-    ok = ok && map_nhwc(&u->grad_map[t], u->grad[t], C, W, H, max_batch, std::min(64, C), bx, by) &&
-         map_nhwc(&u->wg_act[t], u->act[t], C, W, H, max_batch, 64, bxk, byk) &&
-         map_nhwc(&u->wg_grad[t], u->grad[t], C, W, H, max_batch, 64, bxk, byk);
+    ok = ok && map_nhwc(&u->grad_map[t], u->grad[t], C, W, H, max_batch, std::min(64, C), 16, 10) &&
+         map_nhwc(&u->wg_act[t], u->act[t], C, W, H, max_batch, 64, 8, 10) &&
+         map_nhwc(&u->wg_grad[t], u->grad[t], C, W, H, max_batch, 64, 8, 8);
   }
   if (!ok) {
     unet_free(u);
