@@ -91,7 +91,7 @@ constexpr int layer_cin(int l) {
 // ---------------------------------------------------------------------------
 struct ConvArgs {
   CUtensorMap in_map[2];  // activations: 4-D [C, W+2, H+2, B], box [KC, BX, BY, 1]
-  CUtensorMap w_map;      // weights: 2-D [9 Cin_tot, rows], box [KC, BN]
+  CUtensorMap w_map;      // weights: 4-D [Cin_tot, rows, 3 dy, 3 dx], box [KC, BN, 3, 1]
   int nin, cin[2], koff[2], cin_tot;
   int H, W;
   int cout;               // output channels
@@ -109,34 +109,33 @@ struct ConvArgs {
   int* err;
 };
 
-// A convolution tile is 128 output pixels, 16 wide and 8 high. For every
-// input, chunk of KC channels and column shift sx in {-1, 0, 1}, one TMA copy
-// brings the 16 x 10 pixels of that shift (rows y0 - 1 .. y0 + 8): a K-major
-// operand of 160 rows whose rows 16 (sy + 1) .. + 127 are the tile's pixels
-// shifted by (sx, sy). The three row shifts share the copy (an offset of 16
-// rows is a whole number of swizzle atoms) and each takes the weights of
-// its own tap, one copy of BN x KC. Two rings of stages: shifted pixels (A)
-// and weights (B).
+// A convolution tile is 128 output pixels, 16 wide and 8 high. A stage
+// holds, for one input, chunk of KC channels and column shift sx in
+// {-1, 0, 1}: the 16 x 10 pixels of that shift (rows y0 - 1 .. y0 + 8), a
+// K-major operand of 160 rows whose rows 16 (sy + 1) .. + 127 are the
+// tile's pixels shifted by (sx, sy), and the BN x KC weights of the three
+// taps with that column shift, all by two TMA copies. The three row shifts
+// read the pixels at offsets of 16 rows, whole swizzle atoms.
 template <int KC, int BN>
 struct ConvShape {
   static constexpr int TW = 16, TH = 8;        // the tile of output pixels
   static constexpr int AROWS = TW * (TH + 2);  // rows of a shifted box
   static constexpr int ABYTES = AROWS * KC * 2, BBYTES = BN * KC * 2;
   static constexpr int ASTRIDE = (ABYTES + 1023) / 1024 * 1024;
-  static constexpr int BSTRIDE = (BBYTES + 1023) / 1024 * 1024;
-  static constexpr int STA = 4;
-  static constexpr int STB0 = (200 * 1024 - STA * ASTRIDE) / BSTRIDE;
-  static constexpr int STB = STB0 > 12 ? 12 : (STB0 < 2 ? 2 : STB0);
-  static constexpr int ACOLS = BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
+  static constexpr int BSTRIDE = BBYTES;       // the weight box's dy blocks are contiguous
+  static constexpr int STAGE = ASTRIDE + (3 * BBYTES + 1023) / 1024 * 1024;
+  static constexpr int ST0 = 204 * 1024 / STAGE;
+  static constexpr int ST = STAGE <= 50 * 1024 ? 4 : (ST0 < 2 ? 2 : ST0);
+  static constexpr int ACOLS = BN <= 32 ? 32 : (BN <= 64 ? 64 : 128);
   static constexpr int TCOLS = 2 * ACOLS;          // two accumulators
   static constexpr int CTAS_TMEM = 512 / TCOLS;    // CTAs whose TMEM fits one SM
-  static constexpr size_t SMEM_NEED =
-      1024 + (size_t)STA * ASTRIDE + (size_t)STB * BSTRIDE + 8 * (2 * STA + 2 * STB + 5) + 16;
+  static constexpr size_t SMEM_NEED = 1024 + (size_t)ST * STAGE + 8 * (2 * ST + 5) + 16;
   // ask for enough shared memory that no more CTAs than CTAS_TMEM share an SM
   static constexpr size_t SMEM_TMEM = 233472 / (CTAS_TMEM + 1) + 1024;
   static constexpr size_t SMEM = SMEM_NEED > SMEM_TMEM ? SMEM_NEED : SMEM_TMEM;
+  static_assert(BN <= 128, "output-channel tiles of at most 128");
   static_assert(SMEM_NEED <= 232448, "stages exceed shared memory");
-  static_assert((16 * KC * 2) % (8 * KC * 2) == 0, "row shifts are whole swizzle atoms");
+  static_assert(BBYTES % (8 * KC * 2) == 0, "weight blocks are whole swizzle atoms");
 };
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
@@ -150,19 +149,15 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 // Work item w of the CTA is tile w / ntn, output-channel tile w % ntn, for
 // w = blockIdx.x, + gridDim.x, ...
 template <int KC, int BN>
-__global__ void __launch_bounds__(192) conv_tc(const __grid_constant__ ConvArgs a, int ntn) {
+__global__ void __launch_bounds__(192, 1) conv_tc(const __grid_constant__ ConvArgs a, int ntn) {
   using S = ConvShape<KC, BN>;
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-  unsigned char* sA = sm;
-  unsigned char* sB = sm + S::STA * S::ASTRIDE;
-  uint64_t* fullA = (uint64_t*)(sB + S::STB * S::BSTRIDE);
-  uint64_t* emptyA = fullA + S::STA;
-  uint64_t* fullB = emptyA + S::STA;
-  uint64_t* emptyB = fullB + S::STB;
-  uint64_t* tfull = emptyB + S::STB;  // [2] accumulator ready
-  uint64_t* tempty = tfull + 2;       // [2] accumulator drained
-  uint64_t* drain = tempty + 2;       // every MMA of this CTA has completed
+  uint64_t* full = (uint64_t*)(sm + S::ST * S::STAGE);
+  uint64_t* empty = full + S::ST;
+  uint64_t* tfull = empty + S::ST;  // [2] accumulator ready
+  uint64_t* tempty = tfull + 2;     // [2] accumulator drained
+  uint64_t* drain = tempty + 2;     // every MMA of this CTA has completed
   uint32_t* tslot = (uint32_t*)(drain + 1);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int W = a.W, H = a.H;
@@ -171,13 +166,9 @@ __global__ void __launch_bounds__(192) conv_tc(const __grid_constant__ ConvArgs 
   const int sgn = a.reverse_taps ? -1 : 1;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < S::STA; ++s) {
-      mbar_init(&fullA[s], 1);
-      mbar_init(&emptyA[s], 1);
-    }
-    for (int s = 0; s < S::STB; ++s) {
-      mbar_init(&fullB[s], 1);
-      mbar_init(&emptyB[s], 1);
+    for (int s = 0; s < S::ST; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
     }
     for (int j = 0; j < 2; ++j) {
       mbar_init(&tfull[j], 1);
@@ -194,38 +185,32 @@ __global__ void __launch_bounds__(192) conv_tc(const __grid_constant__ ConvArgs 
   bool ok = true;
   if (warp == 0) {
     if (lane == 0) {
-      int ka = 0, kb = 0;  // stage counters over all items
+      int k = 0;  // stage counter over all items
       for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
         const int tile = item / ntn, n0 = (item % ntn) * BN;
         const int b = tile / tpi, r = tile % tpi;
         const int x0 = (r % tpr) * S::TW, y0 = (r / tpr) * S::TH;
         for (int i = 0; i < a.nin && ok; ++i)
           for (int c0 = 0; c0 < a.cin[i] && ok; c0 += KC)
-            for (int sx = -1; sx <= 1 && ok; ++sx, ++ka) {
-              const int sa = ka % S::STA, ita = ka / S::STA;
-              if (ita > 0) ok = mbar_wait_bounded(&emptyA[sa], (ita - 1) & 1);
+            for (int sx = -1; sx <= 1 && ok; ++sx, ++k) {
+              const int s = k % S::ST, it = k / S::ST;
+              if (it > 0) ok = mbar_wait_bounded(&empty[s], (it - 1) & 1);
               if (!ok) break;
-              mbar_arrive_expect_tx(&fullA[sa], (uint32_t)S::ABYTES);
+              unsigned char* st = sm + s * S::STAGE;
+              mbar_arrive_expect_tx(&full[s], (uint32_t)(S::ABYTES + 3 * S::BBYTES));
               // halo coordinates: real column x0 + sx is x0 + sx + 1, real
               // row y0 - 1 is y0
-              tma_load_4d(sA + sa * S::ASTRIDE, &a.in_map[i], &fullA[sa], c0, x0 + sx + 1, y0, b);
-              for (int sy = -1; sy <= 1 && ok; ++sy, ++kb) {
-                const int sb = kb % S::STB, itb = kb / S::STB;
-                if (itb > 0) ok = mbar_wait_bounded(&emptyB[sb], (itb - 1) & 1);
-                if (!ok) break;
-                // the tap whose pixel is at shift (sx, sy)
-                const int tap = 3 * (sgn * sy + 1) + (sgn * sx + 1);
-                mbar_arrive_expect_tx(&fullB[sb], (uint32_t)S::BBYTES);
-                tma_load_2d(sB + sb * S::BSTRIDE, &a.w_map, &fullB[sb],
-                            tap * a.cin_tot + a.koff[i] + c0, n0);
-              }
+              tma_load_4d(st, &a.in_map[i], &full[s], c0, x0 + sx + 1, y0, b);
+              // the three taps whose pixels are at column shift sx: tap
+              // column sgn sx, rows dy = -1, 0, 1 in that order
+              tma_load_4d(st + S::ASTRIDE, &a.w_map, &full[s], a.koff[i] + c0, n0, 0, sgn * sx + 1);
             }
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_bf16_f32(128, BN);
-      int ka = 0, kb = 0, local = 0;
+      int k = 0, local = 0;
       for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x, ++local) {
         const int ab = local & 1, use = local >> 1;
         if (use > 0) ok = mbar_wait_bounded(&tempty[ab], (use - 1) & 1);
@@ -235,26 +220,27 @@ __global__ void __launch_bounds__(192) conv_tc(const __grid_constant__ ConvArgs 
         uint32_t accumulate = 0;
         for (int i = 0; i < a.nin && ok; ++i)
           for (int c0 = 0; c0 < a.cin[i] && ok; c0 += KC)
-            for (int sx = 0; sx < 3 && ok; ++sx, ++ka) {
-              const int sa = ka % S::STA, ita = ka / S::STA;
-              ok = mbar_wait_bounded(&fullA[sa], ita & 1);
+            for (int sx = 0; sx < 3 && ok; ++sx, ++k) {
+              const int s = k % S::ST, it = k / S::ST;
+              ok = mbar_wait_bounded(&full[s], it & 1);
               if (!ok) break;
-              for (int sy = 0; sy < 3 && ok; ++sy, ++kb) {
-                const int sb = kb % S::STB, itb = kb / S::STB;
-                ok = mbar_wait_bounded(&fullB[sb], itb & 1);
-                if (!ok) break;
-                tc_fence_after();
-                const unsigned char* pa = sA + sa * S::ASTRIDE + sy * S::TW * KC * 2;
-                const unsigned char* pb = sB + sb * S::BSTRIDE;
+              tc_fence_after();
+              const unsigned char* st = sm + s * S::STAGE;
+#pragma unroll
+              for (int sy = 0; sy < 3; ++sy) {
+                // pixels at row shift sy - 1 take the weights of tap row
+                // sgn (sy - 1), block sgn (sy - 1) + 1 of the weight box
+                const int wb = a.reverse_taps ? 2 - sy : sy;
+                const unsigned char* pa = st + sy * S::TW * KC * 2;
+                const unsigned char* pb = st + S::ASTRIDE + wb * S::BSTRIDE;
 #pragma unroll
                 for (int kk = 0; kk < KC / 16; ++kk) {
                   tc_mma(acc, sdesc_kmajor<KC * 2>(pa + kk * 32), sdesc_kmajor<KC * 2>(pb + kk * 32),
                          idesc, accumulate);
                   accumulate = 1;
                 }
-                tc_commit(&emptyB[sb]);
               }
-              tc_commit(&emptyA[sa]);
+              tc_commit(&empty[s]);
             }
         tc_commit(&tfull[ab]);
       }
@@ -379,6 +365,14 @@ struct WgShape {
   static_assert(3 * BN <= 512, "three accumulators must fit the tensor memory");
 };
 
+// dst[0..3] += v[0..3] (FP32 bit patterns), one 16-byte vector reduction in
+// the L2; dst 16-byte aligned
+__device__ __forceinline__ void red_add_v4(float* dst, const uint32_t* v) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst), "f"(__uint_as_float(v[0])),
+               "f"(__uint_as_float(v[1])), "f"(__uint_as_float(v[2])), "f"(__uint_as_float(v[3]))
+               : "memory");
+}
+
 template <int BN>
 __global__ void __launch_bounds__(128) wgrad_tc(const __grid_constant__ WgradArgs a) {
   using S = WgShape<BN>;
@@ -464,12 +458,10 @@ __global__ void __launch_bounds__(128) wgrad_tc(const __grid_constant__ WgradArg
       for (int c = 0; c < BN; c += 16) {
         uint32_t rr[16];
         tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(j * BN + c), rr);
-        if (o >= a.cout) continue;
-        for (int i = 0; i < 16; ++i) {
-          const int ci = c0 + c + i;
-          if (ci < a.cin)
-            atomicAdd(a.dw + ((long)o * 9 + tap) * a.cin_tot + a.koff + ci, __uint_as_float(rr[i]));
-        }
+        if (o >= a.cout || c0 + c >= a.cin) continue;  // cin is a multiple of 16
+        float* dst = a.dw + ((long)o * 9 + tap) * a.cin_tot + a.koff + c0 + c;
+#pragma unroll
+        for (int i = 0; i < 16; i += 4) red_add_v4(dst + i, rr + i);
       }
     }
   } else if (!dok && threadIdx.x == 0) {
@@ -877,14 +869,17 @@ bool map_nhwc(CUtensorMap* m, void* base, int C, int W, int H, int B, int bc, in
 }
 
 // 2-D map of a weight matrix [rows][K] (K contiguous), box [kc, bn]
+// weights [rows][tap][K] (tap = 3 (dy + 1) + (dx + 1)) as a 4-D tensor
+// [K, rows, 3 dy, 3 dx]; a box [kc, bn, 3, 1] holds one tap column's three
+// taps, each a K-major bn x kc block
 bool map_weights(CUtensorMap* m, void* base, int K, int rows, int kc, int bn) {
   EncodeFn fn = encoder();
   if (!fn) return false;
-  cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
-  cuuint64_t st[1] = {(cuuint64_t)K * 2};
-  cuuint32_t box[2] = {(cuuint32_t)kc, (cuuint32_t)bn};
-  cuuint32_t es[2] = {1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, st, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+  cuuint64_t dims[4] = {(cuuint64_t)K, (cuuint64_t)rows, 3, 3};
+  cuuint64_t st[3] = {(cuuint64_t)K * 2 * 9, (cuuint64_t)K * 2 * 3, (cuuint64_t)K * 2};
+  cuuint32_t box[4] = {(cuuint32_t)kc, (cuuint32_t)bn, 3, 1};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, base, dims, st, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
             swizzle_of(kc * 2), CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
          CUDA_SUCCESS;
 }
@@ -899,8 +894,9 @@ int kc_bwd(int l) { return std::min(64, kNet[l].cout); }
 int bn_bwd(int l) {
   int bn = kTC[kNet[l].in[0]];
   if (kNet[l].in[1] >= 0) bn = std::min(bn, kTC[kNet[l].in[1]]);
-  return std::min(bn, 256);
+  return std::min(bn, 128);
 }
+int bn_fwd(int l) { return std::min(kNet[l].cout, 128); }
 int bn_wgrad(int cin) { return cin <= 64 ? 64 : 128; }
 
 template <int KC, int BN>
@@ -915,10 +911,10 @@ cudaError_t launch_conv_t(const ConvArgs& a, int ntn, int num_sms, cudaStream_t 
   if (!attr[dev]) {
     e = cudaFuncSetAttribute(conv_tc<KC, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
     if (e != cudaSuccess) return e;
-    int nb = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, conv_tc<KC, BN>, 192, S::SMEM);
-    if (e != cudaSuccess) return e;
-    per_sm[dev] = std::max(1, std::min(nb, S::CTAS_TMEM));
+    // CTAs per SM by shared memory (228 KB, 1 KB reserved per CTA) and by
+    // tensor memory
+    const int by_smem = 233472 / ((int)S::SMEM + 1024);
+    per_sm[dev] = std::max(1, std::min(by_smem, S::CTAS_TMEM));
     attr[dev] = true;
   }
   const int items = a.B_tiles * ntn;
@@ -937,7 +933,6 @@ cudaError_t launch_conv(int kc, int bn, const ConvArgs& a, int ntn, int num_sms,
   MLSW_CONV_CASE(64, 32)
   MLSW_CONV_CASE(64, 64)
   MLSW_CONV_CASE(64, 128)
-  MLSW_CONV_CASE(64, 256)
 #undef MLSW_CONV_CASE
   return cudaErrorInvalidValue;
 }
@@ -1065,7 +1060,7 @@ cudaError_t conv_forward(mlswlbm_unet* u, int l, int batch) {
   }
   a.err = u->err;
   a.B_tiles = batch * (a.W / 16) * (a.H / 8);
-  return launch_conv(kc_fwd(l), N.cout, a, 1, u->num_sms, u->stream);
+  return launch_conv(kc_fwd(l), bn_fwd(l), a, N.cout / bn_fwd(l), u->num_sms, u->stream);
 }
 
 // input gradient of layer l: from grad of its output to the gradients of its
@@ -1124,8 +1119,9 @@ cudaError_t weight_grad(mlswlbm_unet* u, int l, int batch) {
     const int bn = bn_wgrad(a.cin);
     const int mt = (a.cout + 127) / 128, nt = (a.cin + bn - 1) / bn;
     const long chunks = (long)batch * H * W / 64;
-    // about two CTAs per SM over the three column shifts and all tiles
-    const long want = std::max(1L, (long)2 * u->num_sms / (3L * mt * nt));
+    // one CTA per SM over the three column shifts and all tiles (every CTA
+    // adds its whole partial dW: fewer, longer CTAs mean fewer reductions)
+    const long want = std::max(1L, (long)u->num_sms / (3L * mt * nt));
     const int per = (int)std::max(1L, (chunks + want - 1) / want);
     const dim3 grid((unsigned)((chunks + per - 1) / per), (unsigned)(3 * mt), (unsigned)nt);
     a.chunks_per_cta = per;
@@ -1368,8 +1364,8 @@ int mlswlbm_unet_create(int n_layers, int nx, int ny, int max_batch, int n_extra
       w += (size_t)9 * L.cout * L.cin;
       L.wd = w;
       w += (size_t)9 * L.cout * L.cin;
-      ok = map_weights(&u->wf_map[l], L.wf, 9 * L.cin, L.cout, kc_fwd(l), L.cout) &&
-           map_weights(&u->wd_map[l], L.wd, 9 * L.cout, L.cin, kc_bwd(l), bn_bwd(l));
+      ok = map_weights(&u->wf_map[l], L.wf, L.cin, L.cout, kc_fwd(l), bn_fwd(l)) &&
+           map_weights(&u->wd_map[l], L.wd, L.cout, L.cin, kc_bwd(l), bn_bwd(l));
     }
   }
   for (int t = 0; t < kTensors && ok; ++t) {
