@@ -637,6 +637,9 @@ def sweep_workload(B, torch):
         res["create_s"] = time.perf_counter() - t0
         rows = [b.tile_rows(j) for j in range(len(inst))]
         res["groups"] = b.groups()
+        l0 = b.launch_count()
+        b.step(1)
+        res["launches_per_step"] = b.launch_count() - l0
         res["tile_rows_16"] = rows.count(16)
         res["tile_rows_8"] = rows.count(8)
         b.step(3)

@@ -364,11 +364,14 @@ int mlswlbm_diagnostics_noalloc(const mlsw_params* p, const float* f, const floa
  * Batches: many independent D2Q9 lattices (e.g. the instances of a
  * stability or equilibrium sweep: layer counts, sizes and parameters may all
  * differ) advanced together. One step of a batch is one persistent kernel
- * launch per group of instances sharing the layer count, the kernel mode
- * (tau = 1 or not, exponents (3, 2), spreading only between neighbouring
- * interfaces) and the tile height; the groups' launches of a step are
- * captured once in a CUDA graph and replayed. Each instance is stepped with
- * exactly the arithmetic of mlswlbm_step.
+ * launch over a table of every instance's tiles, in which the instances
+ * sharing the layer count, the kernel mode (tau = 1 or not, exponents
+ * (3, 2), spreading only between neighbouring interfaces) and the tile
+ * height (a group) form a contiguous range; CTAs draw tiles from one
+ * counter and pass from range to range without waiting for each other.
+ * The launch is captured once in a CUDA graph per buffer parity and
+ * replayed. Each instance is stepped with exactly the arithmetic of
+ * mlswlbm_step (section LBM, Eq. BGK).
  * ------------------------------------------------------------------------
  */
 typedef struct mlsw_batch mlsw_batch;
@@ -430,7 +433,8 @@ int mlswlbm_batch_tile_rows(const mlsw_batch* b, int index);
 int mlswlbm_batch_select(mlsw_batch* b, int nsel, const int* indices);
 
 /* Kernel launches issued since create (graph replays counted by the
- * kernels they contain), and groups (launches per step). */
+ * kernels they contain: one per step), and groups (ranges of the step's
+ * tile table). */
 long mlswlbm_batch_launch_count(const mlsw_batch* b);
 int mlswlbm_batch_groups(const mlsw_batch* b);
 

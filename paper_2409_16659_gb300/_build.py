@@ -17,9 +17,9 @@ CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libmlswlbm.so")
 DEBUG_LIB = os.path.join(OUT_DIR, "libmlswlbm_debug.so")
-SOURCES = ["mlswlbm.cu", "step_kernels.cu", "aux_kernels.cu", "noalloc.cu", "batch.cu",
-           "analysis.cu", "unet.cu"]
-HEADERS = ["physics.cuh", "kernels.h", "tma.cuh", "tcgen05.cuh", "host.h"]
+SOURCES = ["mlswlbm.cu", "step_kernels.cu", "batch_kernels.cu", "aux_kernels.cu", "noalloc.cu",
+           "batch.cu", "analysis.cu", "unet.cu"]
+HEADERS = ["physics.cuh", "d2q9_tile.cuh", "kernels.h", "tma.cuh", "tcgen05.cuh", "host.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 CFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",

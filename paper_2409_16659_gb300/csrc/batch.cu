@@ -1,9 +1,10 @@
 // batch.cu -- batches of independent D2Q9 lattices (the C ABI's
 // mlswlbm_batch_*): one population arena, per-instance device descriptors,
-// a tile table per group of instances that share layer count, kernel mode
-// and tile height, one persistent launch per group and step, the step's
-// launches captured once in a CUDA graph, and a timing autotuner for the
-// tile height of every class of alike instances.
+// one tile table in which the instances that share layer count, kernel mode
+// and tile height (a group) have a contiguous range, one persistent launch
+// per step over the whole table (batch_kernels.cu), captured once in a CUDA
+// graph, and a timing autotuner for the tile height of every class of
+// alike instances.
 #include <algorithm>
 #include <cstring>
 #include <map>
@@ -22,7 +23,7 @@ using mlsw::KParams;
 namespace {
 
 constexpr int kQ = 9;
-constexpr int kMaxGroups = 5 * 3 * mlsw::kBatchVariants;  // n x mode x variant
+constexpr int kMaxGroups = mlsw::kBatchKinds;  // n x mode x variant
 
 struct Group {
   int n, mode, variant;
@@ -41,17 +42,15 @@ struct mlsw_batch {
   std::vector<int> home;
   std::vector<Group> groups;
   BatchInst* dinst;
-  int2* dtable;
+  int2* dtable;  // the tile table, sorted by kind
   float* arena;
-  int* dstatus;  // [0] error bits, then two scheduler counters per group
+  int* dstatus;  // [0] error bits, [1], [2] the step kernel's tile counters
   float* hbuf;   // heights of the largest instance (upload, read-out)
   int* dk;       // 2 count mode numbers
   double* dmode; // 2 kMaxLayers count doubles
   int cur;
   cudaStream_t stream;   // the caller's stream
   cudaStream_t cap;      // private stream the step graph is captured on
-  cudaStream_t side[kMaxGroups];
-  cudaEvent_t ev[2 * kMaxGroups + 1];
   cudaGraphExec_t gexec[2];  // one step from buffer 0, from buffer 1
   long launches;
   int num_sms;
@@ -109,7 +108,26 @@ int init_all(mlsw_batch* b, const float* const* h_init) {
   return MLSW_OK;
 }
 
-// tile tables of the groups for the current variant choice
+// ends of the groups' ranges of the tile table, per kind (the groups come
+// in kind order: the map below orders them by (n, mode, variant))
+mlsw::BatchEnds ends_of(const mlsw_batch* b) {
+  mlsw::BatchEnds E;
+  int g = 0, end = 0;
+  for (int k = 0; k < mlsw::kBatchKinds; ++k) {
+    if (g < (int)b->groups.size()) {
+      const Group& G = b->groups[g];
+      if (mlsw::batch_kind(G.n, G.mode, G.variant) == k) {
+        end = G.offset + G.ntiles;
+        ++g;
+      }
+    }
+    E.end[k] = end;
+  }
+  return E;
+}
+
+// the tile table of the groups for the current variant choice, sorted by
+// kind
 int build_groups(mlsw_batch* b) {
   std::map<std::tuple<int, int, int>, std::vector<int>> members;
   for (int j = 0; j < b->count; ++j) {
@@ -133,6 +151,8 @@ int build_groups(mlsw_batch* b) {
     b->groups.push_back(g);
   }
   if (b->groups.size() > (size_t)kMaxGroups) return MLSW_ERR_UNSUPPORTED;
+  // the ranges must cover the table in kind order
+  if (ends_of(b).end[mlsw::kBatchKinds - 1] != (int)table.size()) return MLSW_ERR_UNSUPPORTED;
   if (b->dtable) cudaFree(b->dtable);
   b->dtable = nullptr;
   if (cudaMalloc(&b->dtable, std::max<size_t>(1, table.size()) * sizeof(int2)) != cudaSuccess)
@@ -141,41 +161,28 @@ int build_groups(mlsw_batch* b) {
   return MLSW_OK;
 }
 
-mlsw::BatchLaunch group_launch(const mlsw_batch* b, int g, int cur) {
-  const Group& G = b->groups[g];
+// the step launch over the groups' table, from buffer cur
+mlsw::BatchLaunch step_launch(const mlsw_batch* b, int cur) {
   mlsw::BatchLaunch a;
-  a.n = G.n;
-  a.mode = G.mode;
-  a.variant = G.variant;
   a.inst = b->dinst;
-  a.table = b->dtable + G.offset;
-  a.ntiles = G.ntiles;
+  a.table = b->dtable;
+  a.ends = ends_of(b);
   a.cur = cur;
   a.status = b->dstatus;
-  a.sched = b->dstatus + 1 + 2 * g;
+  a.sched = b->dstatus + 1;
   a.num_sms = b->num_sms;
   return a;
 }
 
-// Captures one step (every group, from buffer cur) as a graph: group 0 on the
-// capture stream, the others on side streams forked from it and joined back.
+// Captures one step (from buffer cur) as a graph of its one launch.
 int capture_step(mlsw_batch* b, int cur, cudaGraphExec_t* exec) {
-  const int ng = (int)b->groups.size();
-  // configure every kernel (shared-memory limit, occupancy) outside capture
-  for (int g = 0; g < ng; ++g) {
-    mlsw::BatchLaunch a = group_launch(b, g, cur);
-    a.ntiles = 0;
-    CUB(mlsw::launch_batch_step(a, b->cap));
-  }
+  // configure the kernel (shared-memory limit) outside capture
+  mlsw::BatchLaunch a = step_launch(b, cur);
+  mlsw::BatchLaunch none = a;
+  for (int k = 0; k < mlsw::kBatchKinds; ++k) none.ends.end[k] = 0;
+  CUB(mlsw::launch_batch_step(none, b->cap));
   CUB(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
-  bool ok = cudaEventRecord(b->ev[0], b->cap) == cudaSuccess;
-  for (int g = 1; g < ng && ok; ++g) ok = cudaStreamWaitEvent(b->side[g], b->ev[0], 0) == cudaSuccess;
-  for (int g = 0; g < ng && ok; ++g) {
-    cudaStream_t s = g == 0 ? b->cap : b->side[g];
-    ok = mlsw::launch_batch_step(group_launch(b, g, cur), s) == cudaSuccess;
-    if (ok && g > 0) ok = cudaEventRecord(b->ev[g], s) == cudaSuccess;
-  }
-  for (int g = 1; g < ng && ok; ++g) ok = cudaStreamWaitEvent(b->cap, b->ev[g], 0) == cudaSuccess;
+  const bool ok = mlsw::launch_batch_step(a, b->cap) == cudaSuccess;
   cudaGraph_t graph = nullptr;
   const cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
   if (!ok || e != cudaSuccess || !graph) {
@@ -223,12 +230,11 @@ int autotune(mlsw_batch* b) {
         break;
       }
       mlsw::BatchLaunch a;
-      a.n = n;
-      a.mode = mode;
-      a.variant = v;
       a.inst = b->dinst;
       a.table = dt;
-      a.ntiles = (int)table.size();
+      // one range: kinds before this one end at 0, the others at the end
+      const int kind = mlsw::batch_kind(n, mode, v);
+      for (int k = 0; k < mlsw::kBatchKinds; ++k) a.ends.end[k] = k < kind ? 0 : (int)table.size();
       a.status = b->dstatus;
       a.sched = b->dstatus + 1;
       a.num_sms = b->num_sms;
@@ -268,10 +274,6 @@ void mlswlbm_batch_destroy(mlsw_batch* b) {
   cudaStreamSynchronize(b->stream);
   for (int k = 0; k < 2; ++k)
     if (b->gexec[k]) cudaGraphExecDestroy(b->gexec[k]);
-  for (int g = 0; g < kMaxGroups; ++g)
-    if (b->side[g]) cudaStreamDestroy(b->side[g]);
-  for (int k = 0; k < 2 * kMaxGroups + 1; ++k)
-    if (b->ev[k]) cudaEventDestroy(b->ev[k]);
   if (b->cap) cudaStreamDestroy(b->cap);
   cudaFree(b->dinst);
   cudaFree(b->dtable);
@@ -332,7 +334,7 @@ int mlswlbm_batch_create(int count, const mlsw_params* params, const float* cons
     return MLSW_ERR_CUDA;
   }
   b->num_sms = sms > 0 ? sms : 1;
-  const int nstat = 1 + 2 * kMaxGroups;
+  const int nstat = 3;
   bool ok = cudaMalloc(&b->arena, arena_floats * sizeof(float)) == cudaSuccess &&
             cudaMalloc(&b->dinst, (size_t)count * sizeof(BatchInst)) == cudaSuccess &&
             cudaMalloc(&b->dstatus, nstat * sizeof(int)) == cudaSuccess &&
@@ -346,10 +348,6 @@ int mlswlbm_batch_create(int count, const mlsw_params* params, const float* cons
     return MLSW_ERR_NOMEM;
   }
   ok = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess;
-  for (int g = 0; g < kMaxGroups && ok; ++g)
-    ok = cudaStreamCreateWithFlags(&b->side[g], cudaStreamNonBlocking) == cudaSuccess;
-  for (int k = 0; k < 2 * kMaxGroups + 1 && ok; ++k)
-    ok = cudaEventCreateWithFlags(&b->ev[k], cudaEventDisableTiming) == cudaSuccess;
   // zero padding (cells outside the real domains and their ghost rings are
   // read by edge tiles but feed no real cell) and the status words
   ok = ok && cudaMemsetAsync(b->dstatus, 0, nstat * sizeof(int), b->stream) == cudaSuccess &&
@@ -403,7 +401,7 @@ int mlswlbm_batch_step(mlsw_batch* b, long nsteps) {
   if (b->groups.empty()) return MLSW_OK;  // no instance selected
   for (long s = 0; s < nsteps; ++s) {
     CUB(cudaGraphLaunch(b->gexec[b->cur], b->stream));
-    b->launches += (long)b->groups.size();
+    b->launches += 1;
     b->cur ^= 1;
   }
   return MLSW_OK;

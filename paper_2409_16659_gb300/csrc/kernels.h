@@ -42,7 +42,8 @@ cudaError_t launch_step_persistent(const StepLaunch& a, int nsteps, cudaStream_t
 
 // ---------------------------------------------------------------------------
 // Batches: many independent D2Q9 lattices stepped by one persistent launch
-// per group of instances that share n, kernel mode and tile height.
+// over one tile table, in which the tiles of instances that share n, kernel
+// mode and tile height form a contiguous range (batch_kernels.cu).
 // ---------------------------------------------------------------------------
 // Tile heights a batch can use: variant 0 = 16 rows with two rows per
 // thread (n <= 3 only), variant 1 = 8 rows with one row per thread.
@@ -64,17 +65,37 @@ struct BatchInst {
 // exponents (3, 2), spreading only between neighbouring interfaces).
 int step_mode(const KParams& P);
 
-// One batch step of the instances of one group: tiles of table (device,
-// ntiles entries of (instance, tile)), buffers cur -> cur ^ 1.
+// Kind of a range of tiles: layer count n (1..5), kernel mode, tile-height
+// variant (16-row tiles only for n <= 3).
+constexpr int kBatchKinds = 5 * 3 * kBatchVariants;
+__host__ __device__ constexpr int batch_kind(int n, int mode, int variant) {
+  return ((n - 1) * 3 + mode) * kBatchVariants + variant;
+}
+bool batch_kind_valid(int n, int mode, int variant);
+// dynamic shared memory of the tile loop of one kind
+size_t batch_kind_smem(int n, int variant);
+
+// Ends of the ranges of a tile table sorted by kind: the tiles of kind k are
+// the entries [end[k - 1], end[k]) (end[-1] = 0), so end is non-decreasing
+// and a kind without tiles repeats the previous end.
+struct BatchEnds {
+  int end[kBatchKinds];
+};
+
+// One batch step of every instance in a tile table (device, entries of
+// (instance, tile) in ranges), buffers cur -> cur ^ 1: one launch.
 struct BatchLaunch {
-  int n, mode, variant;
   const BatchInst* inst;
   const int2* table;
-  int ntiles, cur;
+  BatchEnds ends;
+  int cur;
   int* status;
-  int* sched;  // two zero-initialised counters of this group
+  int* sched;  // two zero-initialised counters
   int num_sms;
 };
+// With an empty table (every end 0) it only configures the kernel
+// (shared-memory limit, occupancy) on the current device, so that a later
+// launch can be captured.
 cudaError_t launch_batch_step(const BatchLaunch& a, cudaStream_t st);
 
 // out[2 (j kMaxLayers + i) + {0, 1}] = real and imaginary part of
@@ -196,5 +217,6 @@ inline Layout dense_layout(int nx, int ny, int nplanes = 0) {
 unsigned bounds_violations_step();
 unsigned bounds_violations_aux();
 unsigned bounds_violations_analysis();
+unsigned bounds_violations_batch();
 
 }  // namespace mlsw

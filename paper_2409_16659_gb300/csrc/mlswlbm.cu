@@ -896,8 +896,9 @@ int mlswlbm_debug_bounds_violations(unsigned long long* count) {
   if (!count) return MLSW_ERR_ARG;
 #ifdef MLSW_DEBUG
   if (cudaDeviceSynchronize() != cudaSuccess) return MLSW_ERR_CUDA;
-  const unsigned parts[3] = {mlsw::bounds_violations_step(), mlsw::bounds_violations_aux(),
-                             mlsw::bounds_violations_analysis()};
+  const unsigned parts[4] = {mlsw::bounds_violations_step(), mlsw::bounds_violations_aux(),
+                             mlsw::bounds_violations_analysis(),
+                             mlsw::bounds_violations_batch()};
   unsigned long long total = 0;
   for (unsigned v : parts) {
     if (v == ~0u) return MLSW_ERR_CUDA;
