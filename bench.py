@@ -76,7 +76,9 @@ WORKLOAD = "3-layer D2Q9 spinodal film, 1024x1024 periodic, FP32 populations"
 FALLBACK_HBM_GBS = 6800.0
 CHUNK = 50                         # timed steps between two events
 KERNEL_SOURCES = ["paper_2409_16659_gb300/csrc/step_kernels.cu",
-                  "paper_2409_16659_gb300/csrc/physics.cuh"]
+                  "paper_2409_16659_gb300/csrc/d2q9_tile.cuh",
+                  "paper_2409_16659_gb300/csrc/physics.cuh",
+                  "paper_2409_16659_gb300/csrc/tma.cuh"]
 
 
 def kernel_hash():

@@ -284,6 +284,7 @@ struct SingleTiles {
   int ntx, ntiles, rev;
   static constexpr bool kHints = true;  // L2 cache hints (KParams::l2_policy)
   static constexpr bool kChained = false;
+  static constexpr bool kShiftStores = true;  // edge stores: straight store + periodic shifts
   __device__ TileRef operator()(int t) const {
     const int u = rev ? ntiles - 1 - t : t;
     return {P, map, fout, u % ntx, u / ntx};
@@ -300,6 +301,7 @@ struct BatchTiles {
   int cur, ntiles, variant;  // variant: tensor-map set of this tile height
   static constexpr bool kHints = false;  // plain loads and stores
   static constexpr bool kChained = true;
+  static constexpr bool kShiftStores = false;  // edge stores: wrapped store + explicit images
   __device__ TileRef operator()(int t) const {
     const int2 e = table[t];
     const BatchInst& b = inst[e.x];
@@ -353,6 +355,7 @@ __device__ __forceinline__ int d2q9_tile_loop(const Tiles& tiles, int* __restric
   // stores (no hinted instructions at all, which measured faster there):
   // kept output lines would only crowd out the halo rows of other tiles.
   constexpr bool HINTS = Tiles::kHints;
+  constexpr bool SHIFT = Tiles::kShiftStores;  // edge-tile store scheme (phase C)
   const int l2pol = HINTS ? tiles(blockIdx.x).P->l2_policy : (int)kL2None;  // grid <= ntiles
   const uint64_t st_pol = l2pol == kL2None ? pol_evict_normal() : pol_evict_last();
   const uint64_t ld_pol = l2pol == kL2Resident ? pol_evict_first()
@@ -601,33 +604,84 @@ __device__ __forceinline__ int d2q9_tile_loop(const Tiles& tiles, int* __restric
 #pragma unroll
         for (int l = 0; l < W; ++l)
           cbase[l] = fout + (long)(y0 + iyb + l * BY + L.gy) * L.pitch + (gx + L.gx);
-        // per lane: destinations of the three column / row offsets, images
-        int koff[W][Q], dxs[W][3], dys[W][3], xis[W][3], yis[W][3];
-        bool images[W];
+        // Edge tiles of lattices with both sides >= 4 cells: a population
+        // first goes to the padded cell (x + cx, y + cy) itself, as in an
+        // inner tile. That is its destination, or, when it leaves the
+        // domain, the ghost cell imaging its wrapped destination. A
+        // destination column d in {-1, 0, 1} has its other periodic copy at
+        // d + nx, one in {nx - 2, nx - 1, nx} at d - nx (the wrapped real
+        // cell or a ghost image), others none; rows likewise. xsh and ysh
+        // hold these shifts (0: none) per lane and column / row offset.
+        int xsh[W][3], ysh[W][3];
+        bool wimg = false;  // some lane of the warp has a shifted copy
+        // Lattices with a side below 4 cells: wrapped destinations (koff)
+        // only; a separate pass refreshes their ghosts.
+        int koff[W][Q];
+        if (SHIFT && !inner) {
+          bool img = false;
 #pragma unroll
-        for (int l = 0; l < W && !inner; ++l) {
-          const int gy = y0 + iyb + l * BY;
+          for (int l = 0; l < W; ++l) {
+            const int gy = y0 + iyb + l * BY;
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            int dx = gx + c - 1, dy = gy + c - 1;
-            dx += (dx < 0) ? nx : 0;
-            dx -= (dx >= nx) ? nx : 0;
-            dy += (dy < 0) ? ny : 0;
-            dy -= (dy >= ny) ? ny : 0;
-            dxs[l][c] = dx;
-            dys[l][c] = dy;
-            xis[l][c] = image_of(dx, nx);
-            yis[l][c] = image_of(dy, ny);
+            for (int c = 0; c < 3; ++c) {
+              const int dx = gx + c - 1, dy = gy + c - 1;
+              xsh[l][c] = dx < 2 ? nx : (dx >= nx - 2 ? -nx : 0);
+              ysh[l][c] = dy < 2 ? ny * L.pitch : (dy >= ny - 2 ? -ny * L.pitch : 0);
+              img |= valid[l] && (xsh[l][c] != 0 || ysh[l][c] != 0);
+            }
+            if (P.tiny) {
+              int wx[3], wy[3];
+#pragma unroll
+              for (int c = 0; c < 3; ++c) {
+                int dx = gx + c - 1, dy = gy + c - 1;
+                dx += (dx < 0) ? nx : 0;
+                dx -= (dx >= nx) ? nx : 0;
+                dy += (dy < 0) ? ny : 0;
+                dy -= (dy >= ny) ? ny : 0;
+                wx[c] = dx;
+                wy[c] = dy;
+              }
+#pragma unroll
+              for (int k = 0; k < Q; ++k)
+                koff[l][k] = k * (int)L.plane + (wy[Lattice<2>::cy(k) + 1] + L.gy) * L.pitch +
+                             wx[Lattice<2>::cx(k) + 1] + L.gx;
+            }
           }
-          // lattices with a side below 4 cells refresh their ghosts in a
-          // separate pass; the others write the images here
-          images[l] = !P.tiny && ((xis[l][0] != kNoImage) || (xis[l][1] != kNoImage) ||
-                                  (xis[l][2] != kNoImage) || (yis[l][0] != kNoImage) ||
-                                  (yis[l][1] != kNoImage) || (yis[l][2] != kNoImage));
+          // lanes beyond a ragged edge have left this branch
+          wimg = __any_sync(__activemask(), img);
+        }
+        // the batch kernel's edge stores: wrapped destinations (koff) and
+        // their ghost images, written explicitly (store_edge); this form
+        // compiles to faster code for the batch's many inlined kinds
+        int dxs[W][3], dys[W][3], xis[W][3], yis[W][3];
+        bool images[W];
+        if constexpr (!SHIFT) {
+          // per lane: destinations of the three column / row offsets, images
 #pragma unroll
-          for (int k = 0; k < Q; ++k)
-            koff[l][k] = k * (int)L.plane + (dys[l][Lattice<2>::cy(k) + 1] + L.gy) * L.pitch +
-                         dxs[l][Lattice<2>::cx(k) + 1] + L.gx;
+          for (int l = 0; l < W && !inner; ++l) {
+            const int gy = y0 + iyb + l * BY;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              int dx = gx + c - 1, dy = gy + c - 1;
+              dx += (dx < 0) ? nx : 0;
+              dx -= (dx >= nx) ? nx : 0;
+              dy += (dy < 0) ? ny : 0;
+              dy -= (dy >= ny) ? ny : 0;
+              dxs[l][c] = dx;
+              dys[l][c] = dy;
+              xis[l][c] = image_of(dx, nx);
+              yis[l][c] = image_of(dy, ny);
+            }
+            // lattices with a side below 4 cells refresh their ghosts in a
+            // separate pass; the others write the images here
+            images[l] = !P.tiny && ((xis[l][0] != kNoImage) || (xis[l][1] != kNoImage) ||
+                                    (xis[l][2] != kNoImage) || (yis[l][0] != kNoImage) ||
+                                    (yis[l][1] != kNoImage) || (yis[l][2] != kNoImage));
+#pragma unroll
+            for (int k = 0; k < Q; ++k)
+              koff[l][k] = k * (int)L.plane + (dys[l][Lattice<2>::cy(k) + 1] + L.gy) * L.pitch +
+                           dxs[l][Lattice<2>::cx(k) + 1] + L.gx;
+          }
         }
 #pragma unroll
         for (int i = 0; i < N; ++i) {
@@ -672,20 +726,57 @@ __device__ __forceinline__ int d2q9_tile_loop(const Tiles& tiles, int* __restric
             }
             continue;
           }
-          float* obase = fout + (long)i * lplane;
+          if constexpr (!SHIFT) {
+            float* obase = fout + (long)i * lplane;
 #pragma unroll
-          for (int l = 0; l < W; ++l) {
-            if (!valid[l]) continue;
-            if (!images[l]) {
+            for (int l = 0; l < W; ++l) {
+              if (!valid[l]) continue;
+              if (!images[l]) {
+#pragma unroll
+                for (int k = 0; k < Q; ++k)
+                  *chk_global(fout, obase + koff[l][k], L.length()) = Ln::get(fs[k], l);
+              } else {
+#pragma unroll
+                for (int k = 0; k < Q; ++k) {
+                  const int cxi = Lattice<2>::cx(k) + 1, cyi = Lattice<2>::cy(k) + 1;
+                  store_edge(obase + (long)k * L.plane, L, dxs[l][cxi], dys[l][cyi], xis[l][cxi],
+                             yis[l][cyi], Ln::get(fs[k], l));
+                }
+              }
+            }
+            continue;
+          }
+          if (P.tiny) {
+            float* obase = fout + (long)i * lplane;
+#pragma unroll
+            for (int l = 0; l < W; ++l) {
+              if (!valid[l]) continue;
 #pragma unroll
               for (int k = 0; k < Q; ++k)
                 *chk_global(fout, obase + koff[l][k], L.length()) = Ln::get(fs[k], l);
-            } else {
+            }
+            continue;
+          }
 #pragma unroll
-              for (int k = 0; k < Q; ++k) {
-                const int cxi = Lattice<2>::cx(k) + 1, cyi = Lattice<2>::cy(k) + 1;
-                store_edge(obase + (long)k * L.plane, L, dxs[l][cxi], dys[l][cyi], xis[l][cxi],
-                           yis[l][cyi], Ln::get(fs[k], l));
+          for (int l = 0; l < W; ++l) {
+            if (!valid[l]) continue;
+#pragma unroll
+            for (int k = 0; k < Q; ++k) {
+              const int cx = Lattice<2>::cx(k), cy = Lattice<2>::cy(k);
+              const long o = (long)i * lplane + (long)k * L.plane + cy * L.pitch + cx;
+              const float v = Ln::get(fs[k], l);
+              float* dst = chk_global(fout, &cbase[l][o], L.length());
+              if constexpr (HINTS)
+                st_global_hint(dst, v, st_pol);
+              else
+                *dst = v;
+              if (wimg) {
+                const int xs = xsh[l][cx + 1], ys = ysh[l][cy + 1];
+                if (xs) *chk_global(fout, &cbase[l][o + xs], L.length()) = v;
+                if (ys) {
+                  *chk_global(fout, &cbase[l][o + ys], L.length()) = v;
+                  if (xs) *chk_global(fout, &cbase[l][o + xs + ys], L.length()) = v;
+                }
               }
             }
           }
