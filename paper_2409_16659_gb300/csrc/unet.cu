@@ -141,6 +141,14 @@ struct ConvShape {
   static_assert(BBYTES % (8 * KC * 2) == 0, "weight blocks are whole swizzle atoms");
 };
 
+// 32 bytes to global memory in one 256-bit store (dst 32-byte aligned):
+// a lane's 16 BF16 channels fill a whole sector
+__device__ __forceinline__ void st_global_v8(void* dst, const uint32_t (&v)[8]) {
+  asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(dst), "r"(v[0]),
+               "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+               : "memory");
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
   return *reinterpret_cast<uint32_t*>(&h);
@@ -318,10 +326,9 @@ __global__ void __launch_bounds__(192, 1) conv_tc(const __grid_constant__ ConvAr
 #pragma unroll
           for (int ix = 0; ix < 2; ++ix) {
             if (ys[iy] < 0 || xs[ix] < 0) continue;
-            uint4* dst = reinterpret_cast<uint4*>(
-                a.out[o] + (((long)b * (H + 2) + ys[iy]) * (W + 2) + xs[ix]) * C + lc);
-            dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-            dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+            // 32-byte aligned: every tensor is its own allocation, C and lc
+            // are multiples of 16 channels
+            st_global_v8(a.out[o] + (((long)b * (H + 2) + ys[iy]) * (W + 2) + xs[ix]) * C + lc, pk);
           }
       }
       // this accumulator may be reused once every epilogue warp has read it
