@@ -510,6 +510,18 @@ int mlswlbm_unet_debug(mlswlbm_unet* u, int kind, int id, void* out, long bytes)
 
 void mlswlbm_unet_destroy(mlswlbm_unet* u);
 
+/* The height error by which the LBM judges a surrogate window (the largest
+ * height difference between the surrogate's prediction and the LBM's
+ * heights after the same 64 steps from the same state): for each of
+ * `count` items of `elems` FP32 values each (a and b device arrays, the
+ * items contiguous, [count][elems]), out[j] = max_e |a[j][e] - b[j][e]|; a
+ * NaN or infinite difference counts as +inf, so a non-finite prediction
+ * fails any bound. out: device, count floats, caller-owned. Asynchronous on
+ * `stream` (a cudaStream_t, or NULL). Errors: MLSW_ERR_ARG (NULL pointer,
+ * count < 1 or elems < 1), MLSW_ERR_CUDA. */
+int mlswlbm_max_abs_diff(const float* a, const float* b, int count, long elems, float* out,
+                         void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1280,6 +1280,52 @@ cudaError_t adam(mlswlbm_unet* u, double lr, int do_step) {
 
 bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
+// |x - y|, with a NaN or infinite difference as +inf (a window with a
+// non-finite prediction must fail its audit)
+__device__ __forceinline__ float abs_diff_or_inf(float x, float y) {
+  const float d = fabsf(x - y);
+  return d <= 3.402823466e38f ? d : __int_as_float(0x7f800000);
+}
+
+// out[j] (zeroed by the caller; the bits of a non-negative float order as
+// unsigned integers) = max over item j of |a - b|: a grid-stride loop of
+// float4 loads (or scalars when the items are not 16-byte aligned), a
+// warp-shuffle and block maximum, one atomic maximum per block and item.
+__global__ void __launch_bounds__(256) max_abs_diff_kernel(const float* __restrict__ a,
+                                                           const float* __restrict__ b, int count,
+                                                           long elems, int vec,
+                                                           unsigned* __restrict__ out) {
+  __shared__ float wmax[8];
+  for (int j = blockIdx.y; j < count; j += gridDim.y) {
+    const float* pa = a + (long)j * elems;
+    const float* pb = b + (long)j * elems;
+    const long stride = (long)gridDim.x * blockDim.x;
+    float m = 0.f;
+    if (vec) {
+      const float4* qa = reinterpret_cast<const float4*>(pa);
+      const float4* qb = reinterpret_cast<const float4*>(pb);
+      for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < elems / 4; i += stride) {
+        const float4 x = __ldg(qa + i), y = __ldg(qb + i);
+        m = fmaxf(m, fmaxf(fmaxf(abs_diff_or_inf(x.x, y.x), abs_diff_or_inf(x.y, y.y)),
+                           fmaxf(abs_diff_or_inf(x.z, y.z), abs_diff_or_inf(x.w, y.w))));
+      }
+    } else {
+      for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < elems; i += stride)
+        m = fmaxf(m, abs_diff_or_inf(__ldg(pa + i), __ldg(pb + i)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float t = wmax[0];
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) t = fmaxf(t, wmax[w]);
+      atomicMax(out + j, __float_as_uint(t));
+    }
+    __syncthreads();  // wmax is reused by the next item
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -1521,6 +1567,22 @@ void mlswlbm_unet_destroy(mlswlbm_unet* u) {
   if (!u) return;
   cudaStreamSynchronize(u->stream);
   unet_free(u);
+}
+
+int mlswlbm_max_abs_diff(const float* a, const float* b, int count, long elems, float* out,
+                         void* stream) {
+  if (!a || !b || !out || count < 1 || elems < 1) return MLSW_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemsetAsync(out, 0, (size_t)count * sizeof(float), st) != cudaSuccess)
+    return MLSW_ERR_CUDA;
+  const bool vec = elems % 4 == 0 && (reinterpret_cast<uintptr_t>(a) % 16) == 0 &&
+                   (reinterpret_cast<uintptr_t>(b) % 16) == 0;
+  const long work = vec ? elems / 4 : elems;
+  const long bx = std::min<long>((work + 256 * 8 - 1) / (256 * 8), 1024);
+  const dim3 grid((unsigned)std::max<long>(bx, 1), (unsigned)std::min(count, 65535));
+  max_abs_diff_kernel<<<grid, 256, 0, st>>>(a, b, count, elems, vec ? 1 : 0,
+                                            reinterpret_cast<unsigned*>(out));
+  return cudaGetLastError() == cudaSuccess ? MLSW_OK : MLSW_ERR_CUDA;
 }
 
 }  // extern "C"

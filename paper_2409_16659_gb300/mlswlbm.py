@@ -611,10 +611,38 @@ EXPORTS_UNET = {
     "mlswlbm_unet_debug": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_void_p, ctypes.c_long]),
     "mlswlbm_unet_destroy": (None, [ctypes.c_void_p]),
+    "mlswlbm_max_abs_diff": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                            ctypes.c_long, ctypes.c_void_p, ctypes.c_void_p]),
 }
 
 
 EXPORTS.update(EXPORTS_UNET)  # bound by lib() with the others
+
+
+def max_abs_diff(a, b, out=None, stream=None):
+    """mlswlbm_max_abs_diff: per item (first dimension) the largest
+    |a - b| of two float32 contiguous CUDA tensors of one shape, a NaN or
+    infinite difference as +inf. Returns out (a float32 CUDA tensor of the
+    item count), enqueued on `stream` (default: torch's current stream)."""
+    import torch
+    for t in (a, b):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32
+                and t.is_contiguous()):
+            raise ValueError("float32 contiguous CUDA tensors expected")
+    if tuple(a.shape) != tuple(b.shape) or a.dim() < 1 or a.numel() == 0:
+        raise ValueError("a and b must have one non-empty shape")
+    count = int(a.shape[0])
+    if out is None:
+        out = torch.empty(count, dtype=torch.float32, device=a.device)
+    elif not (out.is_cuda and out.dtype == torch.float32 and out.is_contiguous()
+              and out.numel() == count):
+        raise ValueError("out: float32 contiguous CUDA tensor of the item count")
+    st = torch.cuda.current_stream() if stream is None else stream
+    _check(lib().mlswlbm_max_abs_diff(ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(b.data_ptr()),
+                                      count, int(a.numel() // count),
+                                      ctypes.c_void_p(out.data_ptr()), _stream_ptr(st)),
+           "mlswlbm_max_abs_diff")
+    return out
 
 
 UNET_TENSORS = ("X0", "A0", "S0", "P1", "A1", "S1", "P2", "A2", "S2", "P3", "A3", "S3",

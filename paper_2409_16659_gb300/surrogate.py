@@ -140,8 +140,8 @@ def unet_window_errors(u, traj):
         h = h_all[k:k + u.max_batch].contiguous()
         pred = torch.empty_like(h)
         u.predict(h, pred)
-        err.append((pred - t_all[k:k + u.max_batch]).abs().amax(dim=(1, 2, 3)))
-    ident = (t_all - h_all).abs().amax(dim=(1, 2, 3))
+        err.append(B.max_abs_diff(pred, t_all[k:k + u.max_batch].contiguous()))
+    ident = B.max_abs_diff(t_all.contiguous(), h_all.contiguous())
     return (torch.cat(err).cpu().numpy().reshape(ninst, nwin),
             ident.cpu().numpy().reshape(ninst, nwin))
 
@@ -193,7 +193,7 @@ def judged_rollout(u, params, heights, windows, audit_every, bound=1e-3, stream=
                 aud.step(WINDOW)
                 for i in active:
                     aud.get_heights_device(i, lbm_out[i])
-                err = (out - lbm_out[idx]).abs().amax(dim=(1, 2, 3)).cpu().numpy()
+                err = B.max_abs_diff(out, lbm_out[idx].contiguous(), stream=st).cpu().numpy()
                 audited.extend(float(e) for e in err)
                 keep = []
                 for j, i in enumerate(active):

@@ -140,6 +140,7 @@ def test_null_arguments():
     assert L.mlswlbm_status(None) == B.MLSW_ERR_ARG
     assert L.mlswlbm_check_params(None) == B.MLSW_ERR_ARG
     assert L.mlswlbm_launch_count(None) == -1
+    assert L.mlswlbm_max_abs_diff(None, None, 1, 1, None, None) == B.MLSW_ERR_ARG
     L.mlswlbm_destroy(None)
 
 

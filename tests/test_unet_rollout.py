@@ -58,3 +58,37 @@ def test_accepted_windows_keep_every_layer_mass():
     m0 = np.array([x.astype(np.float64).sum(axis=(1, 2)) for x in heights])
     m1 = h.double().sum(dim=(2, 3)).cpu().numpy()
     np.testing.assert_allclose(m1, m0, rtol=1e-6)
+
+
+def test_max_abs_diff_is_the_windows_height_error():
+    """mlswlbm_max_abs_diff, the audit's error, against numpy: float4 and
+    scalar paths (item sizes divisible by 4 or not, an unaligned start),
+    more items than one grid row holds, and a non-finite difference, which
+    must count as +inf so that a non-finite prediction fails any bound."""
+    import torch
+    rng = np.random.default_rng(5)
+
+    def check(a, b):
+        got = B.max_abs_diff(a, b).cpu().numpy()
+        an, bn = a.cpu().numpy(), b.cpu().numpy()
+        want = np.abs(an - bn).reshape(an.shape[0], -1).max(axis=1)
+        want = np.where(np.isfinite(want), want, np.inf).astype(np.float32)
+        assert np.array_equal(got, want)
+
+    for shape in [(5, 3, 64, 64), (3, 7, 5), (1, 1), (70000, 4)]:
+        a = torch.from_numpy(rng.normal(size=shape).astype(np.float32)).cuda()
+        b = torch.from_numpy(rng.normal(size=shape).astype(np.float32)).cuda()
+        check(a, b)
+    # an item starting off the 16-byte boundary takes the scalar path
+    base = torch.from_numpy(rng.normal(size=4 * 1024 + 1).astype(np.float32)).cuda()
+    other = torch.from_numpy(rng.normal(size=4 * 1024).astype(np.float32)).cuda()
+    check(base[1:].view(4, 1024), other.view(4, 1024))
+    # NaN and inf in item 1 only; equal items give exactly 0
+    a = torch.from_numpy(rng.normal(size=(3, 2, 16, 16)).astype(np.float32)).cuda()
+    b = a.clone()
+    b[1, 0, 3, 4] = float("nan")
+    b[1, 1, 0, 0] = float("inf")
+    got = B.max_abs_diff(a, b).cpu().numpy()
+    assert got[0] == 0.0 and got[2] == 0.0 and np.isposinf(got[1])
+    with pytest.raises(ValueError):
+        B.max_abs_diff(a, b[:2].contiguous())
