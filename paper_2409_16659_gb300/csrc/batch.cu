@@ -447,6 +447,41 @@ int mlswlbm_batch_set_heights_device(mlsw_batch* b, int index, const float* dev_
   return MLSW_OK;
 }
 
+int mlswlbm_batch_get_heights_device_many(mlsw_batch* b, int count, const int* indices,
+                                          float* dev_out) {
+  if (!b || count < 0 || (count > 0 && (!indices || !dev_out))) return MLSW_ERR_ARG;
+  for (int k = 0; k < count; ++k)
+    if (indices[k] < 0 || indices[k] >= b->count) return MLSW_ERR_ARG;
+  size_t off = 0;
+  for (int k = 0; k < count; ++k) {
+    const int j = indices[k];
+    const KParams& P = b->hinst[j].P;
+    CUB(mlsw::launch_batch_heights(&b->hinst[j], state_buffer(b, j), dev_out + off, b->stream));
+    b->launches += 1;
+    off += (size_t)P.n * P.nx * P.ny;
+  }
+  return MLSW_OK;
+}
+
+int mlswlbm_batch_set_heights_device_many(mlsw_batch* b, int count, const int* indices,
+                                          const float* dev_in) {
+  if (!b || count < 0 || (count > 0 && (!indices || !dev_in))) return MLSW_ERR_ARG;
+  for (int k = 0; k < count; ++k)
+    if (indices[k] < 0 || indices[k] >= b->count) return MLSW_ERR_ARG;
+  size_t off = 0;
+  for (int k = 0; k < count; ++k) {
+    const int j = indices[k];
+    const KParams& P = b->hinst[j].P;
+    mlsw::KShift sh;
+    for (int i = 0; i < mlsw::kMaxLayers; ++i) sh.H[i] = P.H[i];
+    CUB(mlsw::launch_init(kQ, P.n, P.L, true, dev_in + off, b->hinst[j].f[state_buffer(b, j)],
+                          sh, b->dstatus, b->stream));
+    b->launches += 1;
+    off += (size_t)P.n * P.nx * P.ny;
+  }
+  return MLSW_OK;
+}
+
 int mlswlbm_batch_modes(mlsw_batch* b, const int* kx, const int* ky, double* out) {
   if (!b || !kx || !ky || !out) return MLSW_ERR_ARG;
   const int rc = align_buffers(b);

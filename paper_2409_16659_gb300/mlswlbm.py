@@ -115,6 +115,12 @@ EXPORTS = {
     "mlswlbm_batch_get_heights": (ctypes.c_int, [_H, ctypes.c_int, _F]),
     "mlswlbm_batch_get_heights_device": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_void_p]),
     "mlswlbm_batch_set_heights_device": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_void_p]),
+    "mlswlbm_batch_get_heights_device_many": (ctypes.c_int, [_H, ctypes.c_int,
+                                                             ctypes.POINTER(ctypes.c_int),
+                                                             ctypes.c_void_p]),
+    "mlswlbm_batch_set_heights_device_many": (ctypes.c_int, [_H, ctypes.c_int,
+                                                             ctypes.POINTER(ctypes.c_int),
+                                                             ctypes.c_void_p]),
     "mlswlbm_batch_select": (ctypes.c_int, [_H, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "mlswlbm_batch_modes": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_int),
                                            ctypes.POINTER(ctypes.c_int), _D]),
@@ -512,6 +518,32 @@ class Batch:
         _check(lib().mlswlbm_batch_set_heights_device(
             self._b, int(index), _dev_ptr(h, int(np.prod(self.shapes[index])))),
             "mlswlbm_batch_set_heights_device")
+
+    def _many(self, indices, t):
+        idx = np.ascontiguousarray([int(i) for i in indices], dtype=np.int32)
+        if idx.size and (idx.min() < 0 or idx.max() >= len(self.shapes)):
+            raise ValueError("instance index out of range")
+        elems = sum(int(np.prod(self.shapes[i])) for i in idx)
+        return idx, _dev_ptr(t, elems)
+
+    def get_heights_device_many(self, indices, out):
+        """mlswlbm_batch_get_heights_device_many: out is a float32 CUDA tensor
+        holding the listed instances' heights one after another
+        (asynchronous)."""
+        idx, ptr = self._many(indices, out)
+        _check(lib().mlswlbm_batch_get_heights_device_many(
+            self._b, int(idx.size), idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ptr),
+            "mlswlbm_batch_get_heights_device_many")
+        return out
+
+    def set_heights_device_many(self, indices, h):
+        """mlswlbm_batch_set_heights_device_many: restarts the listed
+        instances at rest from the float32 CUDA tensor h, their heights one
+        after another (asynchronous)."""
+        idx, ptr = self._many(indices, h)
+        _check(lib().mlswlbm_batch_set_heights_device_many(
+            self._b, int(idx.size), idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ptr),
+            "mlswlbm_batch_set_heights_device_many")
 
     def select(self, indices):
         """mlswlbm_batch_select: only these instances advance in later steps;

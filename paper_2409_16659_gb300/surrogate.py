@@ -172,7 +172,6 @@ def judged_rollout(u, params, heights, windows, audit_every, bound=1e-3, stream=
     h = torch.stack([torch.from_numpy(np.asarray(x, dtype=np.float32)) for x in heights]).cuda()
     ckpt = h.clone()
     ckpt_w = [0] * M
-    lbm_out = torch.empty_like(h)
     active = list(range(M))          # instances still on the surrogate
     fallback, audited = {}, []
     taken = [0] * M                  # windows taken from the surrogate since the last audit
@@ -188,24 +187,27 @@ def judged_rollout(u, params, heights, windows, audit_every, bound=1e-3, stream=
             out = torch.empty_like(sub)
             _predict_all(u, sub, out)
             if w == 0 or (w + 1) % audit_every == 0 or w == windows - 1:
-                for j, i in enumerate(active):
-                    aud.set_heights_device(i, sub[j])
+                aud.set_heights_device_many(active, sub)
                 aud.step(WINDOW)
-                for i in active:
-                    aud.get_heights_device(i, lbm_out[i])
-                err = B.max_abs_diff(out, lbm_out[idx].contiguous(), stream=st).cpu().numpy()
+                ref = torch.empty_like(sub)
+                aud.get_heights_device_many(active, ref)
+                err = B.max_abs_diff(out, ref, stream=st).cpu().numpy()
                 audited.extend(float(e) for e in err)
-                keep = []
+                keep, keep_j = [], []
                 for j, i in enumerate(active):
                     if err[j] <= bound:
-                        h[i] = lbm_out[i]
-                        ckpt[i] = lbm_out[i]
                         ckpt_w[i] = w + 1
                         surrogate_windows += taken[i]
                         keep.append(i)
+                        keep_j.append(j)
                     else:
                         fallback[i] = ckpt_w[i]
                     taken[i] = 0
+                if keep:
+                    ki = torch.as_tensor(keep, device="cuda")
+                    kj = torch.as_tensor(keep_j, device="cuda")
+                    h[ki] = ref[kj]
+                    ckpt[ki] = ref[kj]
                 if len(keep) != len(active):
                     aud.select(keep)
                 active = keep
@@ -220,15 +222,16 @@ def judged_rollout(u, params, heights, windows, audit_every, bound=1e-3, stream=
         stages = sorted(set(fallback.values()))
         running = []
         for k, w0 in enumerate(stages):
-            for i, wi in fallback.items():
-                if wi == w0:
-                    aud.set_heights_device(i, ckpt[i])
-                    running.append(i)
+            join = [i for i, wi in fallback.items() if wi == w0]
+            aud.set_heights_device_many(join, ckpt[torch.as_tensor(join, device="cuda")].contiguous())
+            running += join
             aud.select(running)
             w1 = stages[k + 1] if k + 1 < len(stages) else windows
             aud.step(WINDOW * (w1 - w0))
-        for i in running:
-            aud.get_heights_device(i, h[i])
+        if running:
+            fin = torch.empty((len(running),) + tuple(h.shape[1:]), dtype=h.dtype, device="cuda")
+            aud.get_heights_device_many(running, fin)
+            h[torch.as_tensor(running, device="cuda")] = fin
         torch.cuda.synchronize()
         secs = time.perf_counter() - t0
         status = aud.status()

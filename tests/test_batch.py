@@ -201,3 +201,43 @@ def test_selected_instances_step_and_the_others_keep_their_state():
         ip = np.array([0, 0], dtype=np.int32)
         assert B.lib().mlswlbm_batch_select(b._b, 2, ip.ctypes.data_as(
             B.ctypes.POINTER(B.ctypes.c_int))) == B.MLSW_ERR_ARG
+
+
+def test_device_heights_of_many_instances_at_once():
+    """mlswlbm_batch_get/set_heights_device_many equal the one-instance calls
+    (any order of indices), and reject an index out of range."""
+    import torch
+    inst = _mixed_instances()
+    with B.Batch([p for p, _ in inst], [h for _, h in inst]) as b:
+        b.step(7)
+        order = [3, 0, 5, 2]
+        sizes = [int(np.prod(b.shapes[j])) for j in order]
+        many = torch.empty(sum(sizes), dtype=torch.float32, device="cuda")
+        b.get_heights_device_many(order, many)
+        off = 0
+        for j, sz in zip(order, sizes):
+            one = torch.empty(sz, dtype=torch.float32, device="cuda")
+            b.get_heights_device(j, one)
+            assert torch.equal(many[off:off + sz], one), j
+            off += sz
+        # restart the listed instances from their own heights: both calls
+        # give the same states, so the next steps give the same heights
+        b.set_heights_device_many(order, many)
+        b.step(3)
+        got = [b.get_heights(j) for j in order]
+    with B.Batch([p for p, _ in inst], [h for _, h in inst]) as c:
+        c.step(7)
+        off = 0
+        for j, sz in zip(order, sizes):
+            one = torch.empty(sz, dtype=torch.float32, device="cuda")
+            c.get_heights_device(j, one)
+            c.set_heights_device(j, one)
+        c.step(3)
+        for j, g in zip(order, got):
+            assert np.array_equal(c.get_heights(j), g), j
+        with pytest.raises(ValueError):
+            c.get_heights_device_many([len(inst)], torch.empty(1, device="cuda"))
+        import ctypes
+        bad = (ctypes.c_int * 1)(len(inst))
+        assert B.lib().mlswlbm_batch_get_heights_device_many(
+            c._b, 1, bad, ctypes.c_void_p(many.data_ptr())) == B.MLSW_ERR_ARG
