@@ -406,11 +406,12 @@ int mlswlbm_batch_get_heights(mlsw_batch* b, int index, float* out);
 int mlswlbm_batch_get_heights_device(mlsw_batch* b, int index, float* dev);
 int mlswlbm_batch_set_heights_device(mlsw_batch* b, int index, const float* dev);
 
-/* The same for `count` instances in one call (indices: host ints, any order,
- * repeats allowed for get): dev is the concatenation, in list order, of the
- * instances' [n][ny][nx] FP32 heights. One kernel launch per instance, no
- * synchronisation. MLSW_ERR_ARG for an index out of range, count < 0 or a
- * NULL pointer with count > 0; nothing is enqueued then. */
+/* The same for `count` instances in one call (indices: host ints, any order;
+ * an instance listed twice is read twice, or set from its later heights):
+ * dev is the concatenation, in list order, of the instances' [n][ny][nx]
+ * FP32 heights. One kernel launch per instance, no synchronisation.
+ * MLSW_ERR_ARG for an index out of range, count < 0 or a NULL pointer with
+ * count > 0; nothing is enqueued then. */
 int mlswlbm_batch_get_heights_device_many(mlsw_batch* b, int count, const int* indices,
                                           float* dev);
 int mlswlbm_batch_set_heights_device_many(mlsw_batch* b, int count, const int* indices,
