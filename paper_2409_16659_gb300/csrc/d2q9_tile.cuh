@@ -820,7 +820,7 @@ __device__ __forceinline__ int d2q9_tile_loop(const Tiles& tiles, int* __restric
         if (tnext < ntiles) stage_params(tnext, (parity ^ 1u) & 1u);
     }
     t = tnext;
-    }  // the pressure and collision phases
+    }
   }
   if (bad) atomicOr(status, kStatusNonfinite);
   if constexpr (Tiles::kChained) {
