@@ -191,3 +191,27 @@ def test_unet_argument_checks_and_parameter_count():
     assert L.mlswlbm_unet_predict(None, None, None, 1) == B.MLSW_ERR_ARG
     assert L.mlswlbm_unet_train_step(None, None, None, 1, 1e-3, None) == B.MLSW_ERR_ARG
     L.mlswlbm_unet_destroy(None)
+
+
+def test_audit_error_and_many_instance_calls_reject_bad_arguments():
+    """mlswlbm_max_abs_diff and the many-instance batch height calls check
+    their arguments on the host before any device work (and the Python
+    binding checks tensor types and index ranges before calling them)."""
+    import ctypes
+    import torch
+    L = B.lib()
+    p = ctypes.c_void_p(16)
+    assert L.mlswlbm_max_abs_diff(None, p, 1, 1, p, None) == B.MLSW_ERR_ARG
+    assert L.mlswlbm_max_abs_diff(p, p, 0, 1, p, None) == B.MLSW_ERR_ARG
+    assert L.mlswlbm_max_abs_diff(p, p, 1, 0, p, None) == B.MLSW_ERR_ARG
+    idx = (ctypes.c_int * 1)(0)
+    for fn in (L.mlswlbm_batch_get_heights_device_many, L.mlswlbm_batch_set_heights_device_many):
+        assert fn(None, 1, idx, p) == B.MLSW_ERR_ARG
+    with pytest.raises(ValueError):  # host tensors
+        B.max_abs_diff(torch.zeros(2, 3), torch.zeros(2, 3))
+    fake = B.Batch.__new__(B.Batch)  # the index check needs only the shapes
+    fake.shapes = [(3, 8, 8), (2, 4, 4)]
+    with pytest.raises(ValueError):
+        fake._many([0, 2], None)
+    with pytest.raises(ValueError):
+        fake._many([-1], None)
